@@ -1,0 +1,25 @@
+"""FP64 CPU oracle for the MPS two-qubit-gate path -- TEST INFRASTRUCTURE ONLY.
+
+This package is the plain, slow, obviously correct reference that the CUDA path is
+checked against.  Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s
+``cpu_baseline`` leg and ``--impl reference`` arm may import it.  The library in
+``paper_2601_04422_gb300`` never imports it and shares no code with it.
+
+Modules
+-------
+mps    -- the MPS simulator (Eq. 2 state, Eq. 3 one-qubit gates, the merge /
+          gate / SVD / absorb two-qubit update, layers, amplitudes, Pauli
+          expectations, overlaps, canonical forms, perfect sampling).
+dense  -- a direct state-vector simulator (the full contraction of Eq. 1), used
+          to pin ``mps`` on small qubit counts where nothing is truncated.
+
+Every function is complex128 / float64.  The singular value decomposition step
+calls LAPACK through ``numpy.linalg.svd`` (a library primitive).
+
+Parity status: every function is pinned by ``tests/test_oracle_*.py`` against
+the dense simulator, closed forms (GHZ, QFT of a basis state), invariants or
+designed spectra -- except the truncated regime at a degenerate cut, where the
+kept subspace is not unique ("parity unpinned": only singular values and
+discarded weights are compared there).
+"""
+from . import dense, mps  # noqa: F401
