@@ -1,0 +1,204 @@
+/*
+ * tnsim.h -- C ABI of the GB300 (sm_103a) MPS two-qubit-gate library.
+ *
+ * The library applies layers of nearest-neighbour two-qubit gates to a Matrix
+ * Product State held in GPU memory (HBM).  Per gate on the adjacent pair
+ * (q, q+1) it runs the steps of the paper's local two-qubit update (Sec. III.A
+ * "Two Qubit Gate", Sec. III.B simulation_kernel, Fig. 2):
+ *
+ *   merge the two sites over their shared bond, contract the 4x4 gate (Eq. 1),
+ *   take a truncated SVD of the (2 chi_L) x (2 chi_R) result, write the left
+ *   singular vectors into site q and S.V^H into site q+1.
+ *
+ * All gates of a layer act on disjoint pairs and run in the same launches
+ * (Sec. III.B "Parallelizing the TAMM Backend": layers of non-overlapping gates).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Qubit 0 is the leftmost site and the most significant bit of a bitstring.
+ *  - Site q is a tensor (chi_q, 2, chi_{q+1}), row-major, complex, with
+ *    chi_0 = chi_n = 1 (Eq. 2).
+ *  - A two-qubit gate is a 4x4 complex128 matrix, row-major, real and imaginary
+ *    parts interleaved (32 doubles), basis index 2*b_q + b_{q+1}.
+ *  - A one-qubit gate is a 2x2 complex128 matrix, row-major, interleaved (8 doubles).
+ *  - Every function returns a tnsim_status and never throws or aborts across the
+ *    ABI.  On failure tnsim_last_error() returns a thread-local message.
+ *  - Host buffers passed in are read before the call returns; output host
+ *    buffers are owned by the caller.  Device memory of a handle is allocated by
+ *    the library (cudaMalloc) at tnsim_mps_create and freed by tnsim_mps_destroy.
+ *  - Device-side failures (a Jacobi SVD that hit its sweep cap) set a status word
+ *    in device memory; they never trap.  They are reported by the next
+ *    synchronising call.
+ */
+#ifndef TNSIM_H
+#define TNSIM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tnsim_mps tnsim_mps; /* opaque handle */
+
+typedef enum {
+    TNSIM_OK = 0,
+    TNSIM_EINVAL = 1,      /* bad argument; nothing was launched, the state is unchanged */
+    TNSIM_ENOMEM = 2,      /* a device or pinned allocation failed */
+    TNSIM_ECUDA = 3,       /* a CUDA runtime call failed (message has the CUDA error) */
+    TNSIM_ENOCONV = 4,     /* a Jacobi SVD reached max_sweeps; the layer was still applied */
+    TNSIM_ETIMEOUT = 5,    /* reserved: a bounded device wait ran out */
+    TNSIM_EUNSUPPORTED = 6 /* entry point or mode not available in this build */
+} tnsim_status;
+
+typedef enum { TNSIM_C64 = 0, TNSIM_C128 = 1 } tnsim_dtype;
+
+/* How a layer is scheduled on the GPU. */
+typedef enum {
+    TNSIM_SCHED_BATCHED = 0, /* every pair of the layer in the same launches */
+    TNSIM_SCHED_PLAIN = 1    /* one pair at a time (the per-pair comparison path) */
+} tnsim_schedule;
+
+typedef struct {
+    int32_t chi_max;    /* bond-dimension cap, >= 1 (Sec. II.A: truncate to a fixed chi) */
+    double cutoff;      /* relative discarded-weight cutoff in [0, 1); 0 = none */
+    int32_t renormalize;/* 1: rescale kept singular values so sum s^2 is unchanged */
+    int32_t max_sweeps; /* Jacobi sweep cap; 0 = default (40 c64, 60 c128) */
+    double jacobi_tol;  /* rotate a column pair while |g| > tol*sqrt(a*b); 0 = default */
+    int32_t schedule;   /* tnsim_schedule */
+} tnsim_params;
+
+/* Fill *out with the defaults for dtype dt (chi_max 64, cutoff 0, renormalize 1).
+ * Errors: EINVAL if out is NULL or dt unknown. */
+tnsim_status tnsim_params_default(tnsim_dtype dt, tnsim_params* out);
+
+/* Create the state |0...0> on n_qubits >= 2 sites with every bond of dimension 1
+ * (Sec. III.B "Implementations").  dt selects complex64 (FP32 arithmetic) or
+ * complex128 (FP64 arithmetic).  p may be NULL (defaults).  cuda_stream is a
+ * cudaStream_t on which all work of this handle is ordered; NULL makes the
+ * library create and own a non-blocking stream.  Device memory for the sites
+ * (capacity min(2^q, 2^(n-q), chi_max) per bond) and for one layer's workspace
+ * is allocated here on the current device.
+ * Errors: EINVAL (n_qubits < 2, bad params), ENOMEM, ECUDA. */
+tnsim_status tnsim_mps_create(int32_t n_qubits, tnsim_dtype dt, const tnsim_params* p,
+                              void* cuda_stream, tnsim_mps** out);
+
+/* Release every device and host resource of m (NULL is accepted). Synchronises m's stream. */
+tnsim_status tnsim_mps_destroy(tnsim_mps* m);
+
+/* Apply one layer (Sec. III.A "One Qubit Gate" / "Two Qubit Gate", Sec. III.B layers):
+ *   u1  : NULL, or n_qubits one-qubit gates (8 doubles each) applied to every qubit
+ *         BEFORE the two-qubit gates (identity entries are allowed);
+ *   q   : n2 left-qubit indices; the pairs (q[i], q[i]+1) must be disjoint;
+ *   g4x4: n2 two-qubit gates (32 doubles each), host memory.
+ * eps_out (may be NULL) receives the relative discarded weight of each gate,
+ * sum_{j>=k} s_j^2 / sum_j s_j^2.  The call is synchronous: it returns after the
+ * layer finished on the GPU.  Errors: EINVAL (bad pair list, non-finite gate,
+ * n2 < 0; nothing launched), ENOCONV (layer applied, an SVD hit max_sweeps), ECUDA. */
+tnsim_status tnsim_apply_layer(tnsim_mps* m, int32_t n2, const int32_t* q,
+                               const double* g4x4, const double* u1, double* eps_out);
+
+/* Same layer with the gate data already in device memory: g4x4_dev (n2*32 doubles),
+ * u1_dev (n_qubits*8 doubles or NULL); q stays a host array.  eps_dev (device,
+ * n2 doubles, may be NULL) receives the discarded weights.  Asynchronous: work is
+ * only ordered on the handle's stream; device-side status is collected by
+ * tnsim_sync.  Errors: EINVAL (bad pair list; nothing launched), ECUDA. */
+tnsim_status tnsim_apply_layer_device(tnsim_mps* m, int32_t n2, const int32_t* q,
+                                      const double* g4x4_dev, const double* u1_dev,
+                                      double* eps_dev);
+
+/* Apply layers to several independent states in one batched schedule: for each
+ * step t in [0, n_steps), state ms[i] gets the layer described by
+ * (n2[t*n_circ+i], q_ptrs[...], g_ptrs[...], u1_ptrs[...]) -- all host arrays in
+ * the same formats as tnsim_apply_layer (a NULL u1 pointer means no 1q gates;
+ * n2 = 0 and no u1 means the state skips that step).  All states must share the
+ * dtype.  Every step's pairs of every state run in the same launches.  Synchronous.
+ * Errors: EINVAL, ENOCONV, ECUDA. */
+tnsim_status tnsim_apply_layers_batched(tnsim_mps* const* ms, int32_t n_circ, int32_t n_steps,
+                                        const int32_t* n2, const int32_t* const* q_ptrs,
+                                        const double* const* g_ptrs,
+                                        const double* const* u1_ptrs);
+
+/* Wait for the handle's stream and return the sticky device status (OK or ENOCONV),
+ * clearing it.  Errors: ECUDA. */
+tnsim_status tnsim_sync(tnsim_mps* m);
+
+/* Current bond dimensions chi_0..chi_n (n_qubits+1 int32, host).  Synchronises. */
+tnsim_status tnsim_bond_dims(tnsim_mps* m, int32_t* out);
+
+/* Singular values kept on bond b (between sites b-1 and b) by the last SVD that
+ * wrote it, after renormalisation; s_out holds chi_max doubles (host), *k_out the
+ * count (0 if no SVD has written that bond).  Synchronises.  Errors: EINVAL. */
+tnsim_status tnsim_bond_spectrum(tnsim_mps* m, int32_t bond, double* s_out, int32_t* k_out);
+
+/* Copy every site to host as complex128 interleaved, site after site, each
+ * (chi_q, 2, chi_{q+1}) row-major.  cap is the number of doubles out can hold;
+ * *needed (may be NULL) receives the number required.  Synchronises.
+ * Errors: EINVAL if cap is too small (nothing written). */
+tnsim_status tnsim_export_sites(tnsim_mps* m, double* out, int64_t cap, int64_t* needed);
+
+/* Replace the state by host sites in the export layout; dims holds chi_0..chi_n
+ * (chi_0 = chi_n = 1, chi_q within the handle's capacity).  Synchronous.
+ * Errors: EINVAL (dims out of range). */
+tnsim_status tnsim_import_sites(tnsim_mps* m, const int32_t* dims, const double* data);
+
+/* <x|psi> for n_str bitstrings (bits: n_str*n_qubits bytes of 0/1, host, qubit 0
+ * first) -- Eq. 2 with every physical leg fixed.  amps_out: n_str complex128
+ * interleaved (host).  Synchronous.  Errors: EINVAL. */
+tnsim_status tnsim_amplitudes(tnsim_mps* m, int64_t n_str, const uint8_t* bits,
+                              double* amps_out);
+
+/* <psi| P |psi> for n_terms Pauli strings (paulis: n_terms*n_qubits chars from
+ * 'I','X','Y','Z', host).  out: n_terms complex128 interleaved (host).  The state
+ * is not normalised first.  Synchronous.  Errors: EINVAL (bad character). */
+tnsim_status tnsim_expect_pauli(tnsim_mps* m, int32_t n_terms, const char* paulis,
+                                double* out);
+
+/* Gradient of an energy with respect to gate angles: not in this build
+ * (returns EUNSUPPORTED). All pointer arguments are ignored. */
+tnsim_status tnsim_grad(const void* circuit, const double* theta, int32_t n_theta,
+                        const void* hamiltonian, const tnsim_params* p,
+                        double* energy_out, double* grad_out);
+
+/* Work counters accumulated on the device since the previous tnsim_last_stats call
+ * on m (then reset).  visit_rows and rotation_rows weight every examined / rotated
+ * column pair by its column length m = 2 chi_L, so the Jacobi SVD's arithmetic is
+ * 16 visit_rows + 20 rotation_rows real flops (FMA = 2). */
+typedef struct {
+    int64_t gates;         /* two-qubit gates applied */
+    int64_t sweeps;        /* Jacobi sweeps, summed over gates */
+    int64_t rotations;     /* column-pair rotations applied */
+    int64_t pair_visits;   /* column pairs examined */
+    int64_t visit_rows;    /* sum over examined pairs of m */
+    int64_t rotation_rows; /* sum over rotated pairs of m */
+    int64_t theta_cmacs;   /* complex multiply-adds of the merge (2chi_L chi_M 2chi_R per gate) */
+    int64_t right_cmacs;   /* complex multiply-adds of the right site (k 2chi_L 2chi_R per gate) */
+} tnsim_stats;
+
+/* Read (and reset) the counters.  Synchronises.  Errors: EINVAL. */
+tnsim_status tnsim_last_stats(tnsim_mps* m, tnsim_stats* out);
+
+/* Kernel classes timed by the optional profiler, in launch order within a layer. */
+enum { TNSIM_K_SITE1Q = 0, TNSIM_K_THETA = 1, TNSIM_K_JACOBI = 2, TNSIM_K_TRUNCATE = 3,
+       TNSIM_K_LEFT = 4, TNSIM_K_RIGHT = 5, TNSIM_K_COUNT = 6 };
+
+/* Enable (on != 0) or disable per-kernel timing: while enabled every layer records
+ * CUDA events on the handle's stream around each of its kernel launches (no extra
+ * synchronisation).  Disabling drops unread records.  Errors: ECUDA. */
+tnsim_status tnsim_profile_enable(tnsim_mps* m, int32_t on);
+
+/* Sum of the device durations (milliseconds) of every recorded launch per kernel
+ * class since the last read, and the number of launches per class; both arrays
+ * have TNSIM_K_COUNT entries.  Synchronises, then resets.  Errors: EINVAL, ECUDA. */
+tnsim_status tnsim_profile_read(tnsim_mps* m, double* ms, int64_t* launches);
+
+/* Thread-local description of the last failure (empty string if none). */
+const char* tnsim_last_error(void);
+
+/* Library version string. */
+const char* tnsim_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TNSIM_H */

@@ -1,0 +1,17 @@
+"""GB300 (sm_103a) MPS two-qubit-gate library: Python binding of libtnsim.so.
+
+The compute path is the CUDA library built from ``csrc/`` (see ``include/tnsim.h``
+for the C ABI).  This package only marshals arguments; importing it fails loudly
+when the library has not been built -- there is no CPU fallback.
+"""
+from ._abi import (  # noqa: F401
+    TNSIM_C64, TNSIM_C128, TNSIM_SCHED_BATCHED, TNSIM_SCHED_PLAIN, TNSIM_OK, TNSIM_EINVAL,
+    TNSIM_ENOMEM, TNSIM_ECUDA, TNSIM_ENOCONV, TNSIM_ETIMEOUT, TNSIM_EUNSUPPORTED,
+    TnsimError, TnsimConvergenceWarning, lib, lib_path, exported_symbols,
+    tnsim_params, tnsim_params_default, tnsim_mps_create, tnsim_mps_destroy, tnsim_apply_layer,
+    tnsim_apply_layer_device, tnsim_apply_layers_batched, tnsim_sync, tnsim_bond_dims,
+    tnsim_bond_spectrum, tnsim_export_sites, tnsim_import_sites, tnsim_amplitudes,
+    tnsim_expect_pauli, tnsim_grad, tnsim_last_stats, tnsim_last_error, tnsim_version,
+    tnsim_stats, tnsim_profile_enable, tnsim_profile_read, TNSIM_K_NAMES,
+    MPS,
+)

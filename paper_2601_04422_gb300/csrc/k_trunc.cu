@@ -1,0 +1,234 @@
+// Truncation and absorption of the two-qubit update, and the one-qubit update.
+//
+//  k_truncate : one CTA per gate.  Squared column norms of the converged W are the
+//               squared singular values (FP64 accumulation); a bitonic sort orders
+//               them descending (ties: lower column first); the kept rank is
+//                 k = max(1, min(chi_max, #{s_j > eps*max(m,n)*s_max},
+//                                smallest k with sum_{j>=k} s_j^2 <= cutoff*sum s_j^2))
+//               (Sec. II.A: truncate the bond; Sec. III.B: "the bond dimension can be
+//               truncated").  The discarded weight and the renormalisation factor
+//               sqrt(sum s^2 / sum_{j<k} s^2) are FP64.  Writes chi[q+1] = k.
+//  k_left     : new left site = left singular vectors (Sec. III.A "Two Qubit Gate"):
+//               A'[(l,p0), j] = W[(l,p0), perm_j] / s_{perm_j}, a gather + transpose
+//               through a shared-memory tile (coalesced reads and writes).
+//  k_site1q   : A'[l,p',r] = sum_p U[p',p] A[l,p,r]  (Eq. 3), in place.
+#include <float.h>
+
+#include "tnsim_internal.h"
+
+namespace tnsim {
+
+template <typename T> struct EpsT;
+template <> struct EpsT<float> { static constexpr double v = FLT_EPSILON; };
+template <> struct EpsT<double> { static constexpr double v = DBL_EPSILON; };
+
+constexpr int TR_THREADS = 512;
+constexpr int TR_MAXN = 1024;
+
+// a comes after b in the sorted order (descending value, ascending index)
+__device__ __forceinline__ bool after(double ka, int ia, double kb, int ib) {
+    return ka < kb || (ka == kb && ia > ib);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TR_THREADS) k_truncate(const GateDesc* __restrict__ gd) {
+    using C = typename CT<T>::type;
+    const GateDesc& d = gd[blockIdx.x];
+    const int q = d.q;
+    const int chiL = d.chi[q], chiM = d.chi[q + 1], chiR = d.chi[q + 2];
+    const int m = 2 * chiL, n = 2 * chiR;
+    const C* Wm = (const C*)d.W;
+    GateOut* out = d.out;
+
+    __shared__ double key[TR_MAXN];
+    __shared__ int idx[TR_MAXN];
+    __shared__ int s_k;
+    __shared__ double s_scale;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    int P2 = 1;
+    while (P2 < n) P2 <<= 1;
+
+    for (int col = warp; col < n; col += TR_THREADS / 32) {
+        const C* w = Wm + (size_t)col * m;
+        double acc = 0.0;
+        for (int r = lane; r < m; r += 32) {
+            const C v = __ldcg(w + r);
+            acc = fma((double)v.x, (double)v.x, fma((double)v.y, (double)v.y, acc));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) { key[col] = acc; idx[col] = col; }
+    }
+    for (int i = n + tid; i < P2; i += TR_THREADS) { key[i] = -1.0; idx[i] = 0x7fffffff; }
+    __syncthreads();
+
+    for (int kk = 2; kk <= P2; kk <<= 1) {
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+            for (int i = tid; i < P2; i += TR_THREADS) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const double ka = key[i], kb = key[ixj];
+                    const int ia = idx[i], ib = idx[ixj];
+                    const bool up = (i & kk) == 0;
+                    const bool sw = up ? after(ka, ia, kb, ib) : after(kb, ib, ka, ia);
+                    if (sw) { key[i] = kb; key[ixj] = ka; idx[i] = ib; idx[ixj] = ia; }
+                }
+            }
+            __syncthreads();
+        }
+    }
+
+    if (tid == 0) {
+        // totals summed from the smallest value up (the order the tail sums use)
+        double total = 0.0;
+        for (int j = n - 1; j >= 0; --j) total += key[j];
+        int k = 1;
+        double eps = 0.0, scale = 1.0;
+        if (total > 0.0) {
+            const double smax = sqrt(key[0]);
+            const double thr = EpsT<T>::v * (double)max(m, n) * smax;
+            int nonzero = 0;
+            while (nonzero < n && sqrt(key[nonzero]) > thr) ++nonzero;
+            // the rank of an m x n matrix is at most min(m, n); this also bounds the
+            // new site shapes by the slot capacities
+            k = max(1, min(min(d.chi_max, nonzero), min(m, n)));
+            if (d.cutoff > 0.0) {
+                const double lim = d.cutoff * total;
+                double tail = 0.0;
+                int kk = n;
+                for (int j = n - 1; j >= 0; --j) {
+                    if (tail + key[j] <= lim) { tail += key[j]; kk = j; }
+                    else break;
+                }
+                k = max(1, min(k, kk));
+            }
+            double disc = 0.0, kept = 0.0;
+            for (int j = n - 1; j >= k; --j) disc += key[j];
+            for (int j = k - 1; j >= 0; --j) kept += key[j];
+            eps = disc / total;
+            if (d.renorm && kept > 0.0) scale = sqrt(total / kept);
+        }
+        s_k = k;
+        s_scale = scale;
+        out->k = k;
+        out->eps = eps;
+        out->scale = scale;
+        if (d.eps_out) *d.eps_out = eps;
+        d.chi[q + 1] = k;
+        *d.spec_k = k;
+        if (out->status) atomicOr(d.sticky, out->status);
+        typedef unsigned long long u64;
+        atomicAdd(&d.stats[0], 1ull);
+        atomicAdd(&d.stats[1], (u64)out->sweeps);
+        atomicAdd(&d.stats[2], out->rotations);
+        atomicAdd(&d.stats[3], out->visits);
+        atomicAdd(&d.stats[4], out->visits * (u64)m);
+        atomicAdd(&d.stats[5], out->rotations * (u64)m);
+        atomicAdd(&d.stats[6], (u64)m * (u64)chiM * (u64)n);
+        atomicAdd(&d.stats[7], (u64)k * (u64)m * (u64)n);
+    }
+    __syncthreads();
+    const int k = s_k;
+    const double scale = s_scale;
+    for (int j = tid; j < n; j += TR_THREADS) {
+        d.s2[j] = key[j];
+        d.perm[j] = idx[j];
+        if (j < k) d.spectrum[j] = sqrt(key[j]) * scale;
+    }
+}
+
+template <typename T>
+cudaError_t launch_truncate(const GateDesc* d, int n_gates, cudaStream_t s) {
+    if (n_gates <= 0) return cudaSuccess;
+    k_truncate<T><<<n_gates, TR_THREADS, 0, s>>>(d);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_left(const GateDesc* __restrict__ gd) {
+    using C = typename CT<T>::type;
+    const GateDesc& d = gd[blockIdx.z];
+    const int q = d.q;
+    const int chiL = d.chi[q];
+    const int m = 2 * chiL;
+    const int k = d.out->k;
+    const int row0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
+    if (row0 >= m || j0 >= k) return;
+    __shared__ C tile[32][33];
+    const C* Wm = (const C*)d.W;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
+    for (int jj = ty; jj < 32; jj += 8) {
+        const int j = j0 + jj;
+        C v; v.x = 0; v.y = 0;
+        if (j < k && row0 + tx < m) {
+            const int col = d.perm[j];
+            const double s2j = d.s2[j];
+            const T inv = s2j > 0.0 ? (T)(1.0 / sqrt(s2j)) : (T)0;
+            v = Wm[(size_t)col * m + row0 + tx];
+            v.x *= inv; v.y *= inv;
+        }
+        tile[jj][tx] = v;
+    }
+    __syncthreads();
+    C* A = (C*)d.siteA;
+    for (int rr = ty; rr < 32; rr += 8) {
+        const int row = row0 + rr, j = j0 + tx;
+        if (row < m && j < k) A[(size_t)row * k + j] = tile[tx][rr];
+    }
+}
+
+template <typename T>
+cudaError_t launch_left(const GateDesc* d, int n_gates, int m_max, int k_max, cudaStream_t s) {
+    if (n_gates <= 0) return cudaSuccess;
+    dim3 grid((m_max + 31) / 32, (k_max + 31) / 32, n_gates);
+    k_left<T><<<grid, 256, 0, s>>>(d);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_site1q(const Site1Desc* __restrict__ sd) {
+    using C = typename CT<T>::type;
+    const Site1Desc& s = sd[blockIdx.y];
+    const int chiL = s.chi[s.q], chiR = s.chi[s.q + 1];
+    C u[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) { u[i].x = (T)s.u[2 * i]; u[i].y = (T)s.u[2 * i + 1]; }
+    C* A = (C*)s.site;
+    const int total = chiL * chiR;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+        const int l = t / chiR, r = t - l * chiR;
+        C* p0 = A + (size_t)(2 * l) * chiR + r;
+        C* p1 = p0 + chiR;
+        const C a0 = *p0, a1 = *p1;
+        C b0, b1;
+        b0.x = u[0].x * a0.x - u[0].y * a0.y + u[1].x * a1.x - u[1].y * a1.y;
+        b0.y = u[0].x * a0.y + u[0].y * a0.x + u[1].x * a1.y + u[1].y * a1.x;
+        b1.x = u[2].x * a0.x - u[2].y * a0.y + u[3].x * a1.x - u[3].y * a1.y;
+        b1.y = u[2].x * a0.y + u[2].y * a0.x + u[3].x * a1.y + u[3].y * a1.x;
+        *p0 = b0;
+        *p1 = b1;
+    }
+}
+
+template <typename T>
+cudaError_t launch_site1q(const Site1Desc* d, int n_sites, int cap_lr, cudaStream_t s) {
+    if (n_sites <= 0) return cudaSuccess;
+    int bx = (cap_lr + 255) / 256;
+    if (bx > 64) bx = 64;
+    if (bx < 1) bx = 1;
+    dim3 grid(bx, n_sites, 1);
+    k_site1q<T><<<grid, 256, 0, s>>>(d);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_truncate<float>(const GateDesc*, int, cudaStream_t);
+template cudaError_t launch_truncate<double>(const GateDesc*, int, cudaStream_t);
+template cudaError_t launch_left<float>(const GateDesc*, int, int, int, cudaStream_t);
+template cudaError_t launch_left<double>(const GateDesc*, int, int, int, cudaStream_t);
+template cudaError_t launch_site1q<float>(const Site1Desc*, int, int, cudaStream_t);
+template cudaError_t launch_site1q<double>(const Site1Desc*, int, int, cudaStream_t);
+
+}  // namespace tnsim

@@ -1,0 +1,799 @@
+// Host runtime behind the C ABI (include/tnsim.h).
+//
+// Memory layout of one state (all device memory is allocated at create time):
+//  - site arena: site q owns a fixed slot of cap_q * 2 * cap_{q+1} complex elements,
+//    cap_b = min(chi_max, 2^b, 2^(n-b)); the live tensor (chi_q, 2, chi_{q+1}) is
+//    stored densely (row-major) at the start of its slot;
+//  - chi[0..n]: live bond dimensions, read by the kernels at run time and written by
+//    the truncation kernel, so consecutive layers need no host round trip;
+//  - one workspace slot per possible gate of a layer (n/2): theta0 and W, each
+//    (2 capmax)^2 elements, plus the sorted spectrum / permutation of that gate;
+//  - per-bond kept singular values (the spectrum written by the last SVD).
+// The host keeps upper bounds ub_b >= chi_b to size grids; the kernels exit early
+// outside the live dimensions.  Synchronising calls refresh ub from chi.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/tnsim.h"
+#include "tnsim_internal.h"
+
+using namespace tnsim;
+
+namespace {
+
+thread_local std::string g_err;
+
+tnsim_status fail(tnsim_status s, const std::string& msg) {
+    g_err = msg;
+    return s;
+}
+
+#define CUDA_TRY(call)                                                                   \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return fail(TNSIM_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+constexpr int kRing = 4;           // pinned staging slots per state
+constexpr int kMaxChi = 512;       // largest supported chi_max
+
+struct Staging {
+    GateDesc* desc = nullptr;      // pinned
+    Site1Desc* s1 = nullptr;       // pinned
+    double* gates = nullptr;       // pinned: G*32 + n*8 doubles
+    cudaEvent_t done = nullptr;    // recorded after the H2D copies that read this slot
+    bool used = false;
+};
+
+}  // namespace
+
+struct tnsim_mps {
+    int n = 0;
+    tnsim_dtype dt = TNSIM_C64;
+    tnsim_params p{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0;
+    size_t esz = 8;
+    std::vector<int> cap, ub;
+    std::vector<size_t> site_off;  // byte offsets into d_sites
+    int G = 0, capmax = 1;
+    size_t ws_elems = 0;
+    char* d_sites = nullptr;
+    int* d_chi = nullptr;
+    char* d_ws = nullptr;          // G slots * (theta0 | W)
+    double* d_s2 = nullptr;
+    int* d_perm = nullptr;
+    double* d_spec = nullptr;      // (n+1) * chi_max
+    int* d_spec_k = nullptr;       // (n+1)
+    GateOut* d_out = nullptr;      // G
+    GateDesc* d_desc = nullptr;    // G
+    Site1Desc* d_s1 = nullptr;     // n
+    double* d_gates = nullptr;     // G*32 + n*8
+    int* d_sticky = nullptr;
+    unsigned long long* d_stats = nullptr;   // 8 counters (tnsim_stats)
+    GateOut* h_out = nullptr;      // pinned readback
+    int* h_chi = nullptr;          // pinned readback
+    Staging ring[kRing];
+    int ring_pos = 0;
+    // optional per-kernel timing
+    bool prof_on = false;
+    std::vector<cudaEvent_t> ev_pool;
+    struct Rec { int cls; cudaEvent_t a, b; };
+    std::vector<Rec> recs;
+};
+
+namespace {
+
+int cap_of(int n, int b, int chi_max) {
+    const int e = std::min(b, n - b);
+    if (e >= 30) return chi_max;
+    return std::min(chi_max, 1 << e);
+}
+
+tnsim_status check_params(const tnsim_params* p) {
+    if (p->chi_max < 1 || p->chi_max > kMaxChi)
+        return fail(TNSIM_EINVAL, "chi_max must be in [1, 512]");
+    if (!(p->cutoff >= 0.0 && p->cutoff < 1.0)) return fail(TNSIM_EINVAL, "cutoff must be in [0, 1)");
+    if (p->max_sweeps < 0 || p->max_sweeps > 10000) return fail(TNSIM_EINVAL, "bad max_sweeps");
+    if (!(p->jacobi_tol >= 0.0 && p->jacobi_tol < 1.0)) return fail(TNSIM_EINVAL, "bad jacobi_tol");
+    if (p->schedule != TNSIM_SCHED_BATCHED && p->schedule != TNSIM_SCHED_PLAIN)
+        return fail(TNSIM_EINVAL, "bad schedule");
+    return TNSIM_OK;
+}
+
+void free_all(tnsim_mps* m) {
+    cudaFree(m->d_sites); cudaFree(m->d_chi); cudaFree(m->d_ws); cudaFree(m->d_s2);
+    cudaFree(m->d_perm); cudaFree(m->d_spec); cudaFree(m->d_spec_k); cudaFree(m->d_out);
+    cudaFree(m->d_desc); cudaFree(m->d_s1); cudaFree(m->d_gates); cudaFree(m->d_sticky);
+    cudaFree(m->d_stats);
+    cudaFreeHost(m->h_out); cudaFreeHost(m->h_chi);
+    for (auto& r : m->ring) {
+        cudaFreeHost(r.desc); cudaFreeHost(r.s1); cudaFreeHost(r.gates);
+        if (r.done) cudaEventDestroy(r.done);
+    }
+    for (cudaEvent_t e : m->ev_pool) cudaEventDestroy(e);
+    for (auto& r : m->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    m->ev_pool.clear();
+    m->recs.clear();
+    if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);
+}
+
+cudaEvent_t prof_event(tnsim_mps* m) {
+    if (!m->ev_pool.empty()) {
+        cudaEvent_t e = m->ev_pool.back();
+        m->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// Record the start event of a timed launch (no-op when profiling is off).
+cudaEvent_t prof_begin(tnsim_mps* m, cudaStream_t st) {
+    if (!m->prof_on) return nullptr;
+    cudaEvent_t a = prof_event(m);
+    if (a) cudaEventRecord(a, st);
+    return a;
+}
+
+void prof_end(tnsim_mps* m, cudaStream_t st, int cls, cudaEvent_t a) {
+    if (!m->prof_on || !a) return;
+    cudaEvent_t b = prof_event(m);
+    if (!b) return;
+    cudaEventRecord(b, st);
+    m->recs.push_back({cls, a, b});
+}
+
+Staging* acquire_staging(tnsim_mps* m) {
+    Staging* s = &m->ring[m->ring_pos];
+    m->ring_pos = (m->ring_pos + 1) % kRing;
+    if (s->used) cudaEventSynchronize(s->done);
+    s->used = true;
+    return s;
+}
+
+void* site_ptr(tnsim_mps* m, int q) { return m->d_sites + m->site_off[q]; }
+
+// validate a pair list: disjoint adjacent pairs inside the chain
+tnsim_status check_pairs(const tnsim_mps* m, int n2, const int32_t* q) {
+    if (n2 < 0 || n2 > m->G) return fail(TNSIM_EINVAL, "n2 out of range");
+    if (n2 > 0 && !q) return fail(TNSIM_EINVAL, "q is NULL");
+    std::vector<char> used(m->n, 0);
+    for (int i = 0; i < n2; ++i) {
+        if (q[i] < 0 || q[i] >= m->n - 1) return fail(TNSIM_EINVAL, "pair index out of range");
+        if (used[q[i]] || used[q[i] + 1]) return fail(TNSIM_EINVAL, "pairs of a layer must be disjoint");
+        used[q[i]] = used[q[i] + 1] = 1;
+    }
+    return TNSIM_OK;
+}
+
+bool finite_all(const double* v, size_t count) {
+    for (size_t i = 0; i < count; ++i)
+        if (!std::isfinite(v[i])) return false;
+    return true;
+}
+
+double default_tol(const tnsim_mps* m) { return m->p.jacobi_tol; }   // 0 = per-gate default in-kernel
+int default_sweeps(const tnsim_mps* m) {
+    if (m->p.max_sweeps > 0) return m->p.max_sweeps;
+    return m->dt == TNSIM_C64 ? 40 : 60;
+}
+
+// One batch of gates (possibly from several states) through K1..K4.
+struct GateJob {
+    tnsim_mps* m;
+    int q;
+    int slot;                  // workspace slot of m
+    const double* g4;          // device
+    const double* uL;          // device or null
+    const double* uR;
+    double* eps_dev;           // device or null
+};
+
+// Fill and upload the descriptors of a batch of gates (possibly from several states).
+tnsim_status upload_desc(cudaStream_t st, const std::vector<GateJob>& jobs, GateDesc* h_desc,
+                         GateDesc* d_desc, GateOut* d_out_base) {
+    const int ng = (int)jobs.size();
+    if (ng == 0) return TNSIM_OK;
+    for (int i = 0; i < ng; ++i) {
+        const GateJob& j = jobs[i];
+        tnsim_mps* m = j.m;
+        const size_t es = m->esz;
+        char* ws = m->d_ws + (size_t)j.slot * 2 * m->ws_elems * es;
+        GateDesc& d = h_desc[i];
+        std::memset(&d, 0, sizeof(d));
+        d.siteA = site_ptr(m, j.q);
+        d.siteB = site_ptr(m, j.q + 1);
+        d.chi = m->d_chi;
+        d.g4 = j.g4;
+        d.uL = j.uL;
+        d.uR = j.uR;
+        d.theta0 = ws;
+        d.W = ws + m->ws_elems * es;
+        d.s2 = m->d_s2 + (size_t)j.slot * 2 * m->capmax;
+        d.perm = m->d_perm + (size_t)j.slot * 2 * m->capmax;
+        d.spectrum = m->d_spec + (size_t)(j.q + 1) * m->p.chi_max;
+        d.spec_k = m->d_spec_k + (j.q + 1);
+        d.eps_out = j.eps_dev;
+        d.out = d_out_base ? (d_out_base + i) : (m->d_out + j.slot);
+        d.sticky = m->d_sticky;
+        d.stats = m->d_stats;
+        d.cutoff = m->p.cutoff;
+        d.q = j.q;
+        d.chi_max = m->p.chi_max;
+        d.renorm = m->p.renormalize ? 1 : 0;
+    }
+    CUDA_TRY(cudaMemcpyAsync(d_desc, h_desc, sizeof(GateDesc) * ng, cudaMemcpyHostToDevice, st));
+    return TNSIM_OK;
+}
+
+template <typename T>
+tnsim_status launch_gates(cudaStream_t st, const std::vector<GateJob>& jobs, const GateDesc* d_desc,
+                          double tol, int sweeps) {
+    const int ng = (int)jobs.size();
+    if (ng == 0) return TNSIM_OK;
+    int chiL_max = 1, chiR_max = 1, k_max = 1;
+    for (const GateJob& j : jobs) {
+        chiL_max = std::max(chiL_max, j.m->ub[j.q]);
+        chiR_max = std::max(chiR_max, j.m->ub[j.q + 2]);
+        k_max = std::max(k_max, std::min({j.m->cap[j.q + 1], 2 * j.m->ub[j.q], 2 * j.m->ub[j.q + 2]}));
+    }
+    const int m_max = 2 * chiL_max, n_max = 2 * chiR_max;
+    tnsim_mps* pm = jobs[0].m;   // the state whose profiler records this batch
+    cudaEvent_t ev = prof_begin(pm, st);
+    CUDA_TRY(launch_theta<T>(d_desc, ng, chiL_max, chiR_max, st));
+    prof_end(pm, st, TNSIM_K_THETA, ev);
+    ev = prof_begin(pm, st);
+    CUDA_TRY(launch_jacobi<T>(d_desc, ng, m_max, n_max, tol, sweeps, st));
+    prof_end(pm, st, TNSIM_K_JACOBI, ev);
+    ev = prof_begin(pm, st);
+    CUDA_TRY(launch_truncate<T>(d_desc, ng, st));
+    prof_end(pm, st, TNSIM_K_TRUNCATE, ev);
+    ev = prof_begin(pm, st);
+    CUDA_TRY(launch_left<T>(d_desc, ng, m_max, k_max, st));
+    prof_end(pm, st, TNSIM_K_LEFT, ev);
+    ev = prof_begin(pm, st);
+    CUDA_TRY(launch_right<T>(d_desc, ng, k_max, n_max, st));
+    prof_end(pm, st, TNSIM_K_RIGHT, ev);
+    // bounds for the next layer
+    for (const GateJob& j : jobs) {
+        tnsim_mps* m = j.m;
+        m->ub[j.q + 1] = std::min({m->cap[j.q + 1], 2 * m->ub[j.q], 2 * m->ub[j.q + 2]});
+    }
+    return TNSIM_OK;
+}
+
+tnsim_status launch_gates_dt(tnsim_dtype dt, cudaStream_t st, const std::vector<GateJob>& jobs,
+                             const GateDesc* d_desc, double tol, int sweeps) {
+    return dt == TNSIM_C64 ? launch_gates<float>(st, jobs, d_desc, tol, sweeps)
+                           : launch_gates<double>(st, jobs, d_desc, tol, sweeps);
+}
+
+// the one-qubit updates of the qubits outside every pair
+tnsim_status launch_unpaired(tnsim_mps* m, Staging* stg, int n2, const int32_t* q, const double* u1_dev) {
+    std::vector<char> used(m->n, 0);
+    for (int i = 0; i < n2; ++i) used[q[i]] = used[q[i] + 1] = 1;
+    int ns = 0, caplr = 1;
+    for (int s = 0; s < m->n; ++s) {
+        if (used[s]) continue;
+        Site1Desc& d = stg->s1[ns++];
+        d.site = site_ptr(m, s);
+        d.chi = m->d_chi;
+        d.u = u1_dev + (size_t)s * 8;
+        d.q = s;
+        d.pad_ = 0;
+        caplr = std::max(caplr, m->ub[s] * m->ub[s + 1]);
+    }
+    if (ns == 0) return TNSIM_OK;
+    CUDA_TRY(cudaMemcpyAsync(m->d_s1, stg->s1, sizeof(Site1Desc) * ns, cudaMemcpyHostToDevice, m->stream));
+    cudaEvent_t ev = prof_begin(m, m->stream);
+    if (m->dt == TNSIM_C64) CUDA_TRY(launch_site1q<float>(m->d_s1, ns, caplr, m->stream));
+    else CUDA_TRY(launch_site1q<double>(m->d_s1, ns, caplr, m->stream));
+    prof_end(m, m->stream, TNSIM_K_SITE1Q, ev);
+    return TNSIM_OK;
+}
+
+// Enqueue one layer whose gate data is in device memory.
+tnsim_status enqueue_layer(tnsim_mps* m, Staging* stg, int n2, const int32_t* q, const double* g4_dev,
+                           const double* u1_dev, double* eps_dev) {
+    cudaStream_t st = m->stream;
+    if (u1_dev) {
+        tnsim_status s = launch_unpaired(m, stg, n2, q, u1_dev);
+        if (s != TNSIM_OK) return s;
+    }
+    if (n2 == 0) return TNSIM_OK;
+    std::vector<GateJob> jobs(n2);
+    for (int i = 0; i < n2; ++i) {
+        jobs[i].m = m;
+        jobs[i].q = q[i];
+        jobs[i].slot = i;
+        jobs[i].g4 = g4_dev + (size_t)i * 32;
+        jobs[i].uL = u1_dev ? u1_dev + (size_t)q[i] * 8 : nullptr;
+        jobs[i].uR = u1_dev ? u1_dev + (size_t)(q[i] + 1) * 8 : nullptr;
+        jobs[i].eps_dev = eps_dev ? eps_dev + i : nullptr;
+    }
+    CUDA_TRY(cudaMemsetAsync(m->d_out, 0, sizeof(GateOut) * n2, st));
+    const double tol = default_tol(m);
+    const int sweeps = default_sweeps(m);
+    tnsim_status s;
+    s = upload_desc(st, jobs, stg->desc, m->d_desc, nullptr);
+    if (s != TNSIM_OK) return s;
+    if (m->p.schedule == TNSIM_SCHED_PLAIN) {
+        // one pair at a time: each pair is its own launch sequence
+        for (int i = 0; i < n2; ++i) {
+            std::vector<GateJob> one(1, jobs[i]);
+            s = launch_gates_dt(m->dt, st, one, m->d_desc + i, tol, sweeps);
+            if (s != TNSIM_OK) return s;
+        }
+    } else {
+        s = launch_gates_dt(m->dt, st, jobs, m->d_desc, tol, sweeps);
+        if (s != TNSIM_OK) return s;
+    }
+    return TNSIM_OK;
+}
+
+tnsim_status refresh_dims(tnsim_mps* m) {
+    CUDA_TRY(cudaMemcpyAsync(m->h_chi, m->d_chi, sizeof(int) * (m->n + 1), cudaMemcpyDeviceToHost, m->stream));
+    CUDA_TRY(cudaStreamSynchronize(m->stream));
+    for (int b = 0; b <= m->n; ++b) m->ub[b] = m->h_chi[b];
+    return TNSIM_OK;
+}
+
+struct DevGuard {
+    int prev = -1;
+    explicit DevGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DevGuard() { if (prev >= 0) cudaSetDevice(prev); }
+};
+
+}  // namespace
+
+// ===========================================================================
+extern "C" {
+
+const char* tnsim_last_error(void) { return g_err.c_str(); }
+const char* tnsim_version(void) { return "tnsim-gb300 0.1 (sm_103a)"; }
+
+tnsim_status tnsim_params_default(tnsim_dtype dt, tnsim_params* out) {
+    if (!out) return fail(TNSIM_EINVAL, "out is NULL");
+    if (dt != TNSIM_C64 && dt != TNSIM_C128) return fail(TNSIM_EINVAL, "unknown dtype");
+    out->chi_max = 64;
+    out->cutoff = 0.0;
+    out->renormalize = 1;
+    out->max_sweeps = 0;
+    out->jacobi_tol = 0.0;
+    out->schedule = TNSIM_SCHED_BATCHED;
+    return TNSIM_OK;
+}
+
+tnsim_status tnsim_mps_create(int32_t n_qubits, tnsim_dtype dt, const tnsim_params* p,
+                              void* cuda_stream, tnsim_mps** out) {
+    g_err.clear();
+    if (!out) return fail(TNSIM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n_qubits < 2 || n_qubits > (1 << 20)) return fail(TNSIM_EINVAL, "n_qubits must be >= 2");
+    if (dt != TNSIM_C64 && dt != TNSIM_C128) return fail(TNSIM_EINVAL, "unknown dtype");
+    tnsim_params prm;
+    tnsim_params_default(dt, &prm);
+    if (p) prm = *p;
+    tnsim_status s = check_params(&prm);
+    if (s != TNSIM_OK) return s;
+
+    tnsim_mps* m = new (std::nothrow) tnsim_mps();
+    if (!m) return fail(TNSIM_ENOMEM, "host allocation failed");
+    m->n = n_qubits;
+    m->dt = dt;
+    m->p = prm;
+    m->esz = dt == TNSIM_C64 ? 8 : 16;
+    cudaGetDevice(&m->device);
+    m->cap.resize(n_qubits + 1);
+    m->ub.assign(n_qubits + 1, 1);
+    for (int b = 0; b <= n_qubits; ++b) {
+        m->cap[b] = cap_of(n_qubits, b, prm.chi_max);
+        m->capmax = std::max(m->capmax, m->cap[b]);
+    }
+    m->site_off.resize(n_qubits);
+    size_t off = 0;
+    for (int q = 0; q < n_qubits; ++q) {
+        m->site_off[q] = off;
+        size_t bytes = (size_t)m->cap[q] * 2 * m->cap[q + 1] * m->esz;
+        off += (bytes + 255) / 256 * 256;
+    }
+    m->G = n_qubits / 2;
+    m->ws_elems = (size_t)(2 * m->capmax) * (2 * m->capmax);
+    const size_t nG = (size_t)m->G;
+    const size_t gate_doubles = nG * 32 + (size_t)n_qubits * 8;
+
+#define ALLOC(ptr, bytes)                                                        \
+    do {                                                                         \
+        cudaError_t e_ = cudaMalloc((void**)&(ptr), (bytes));                    \
+        if (e_ != cudaSuccess) {                                                 \
+            free_all(m); delete m;                                               \
+            return fail(TNSIM_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e_)); \
+        }                                                                        \
+    } while (0)
+#define HALLOC(ptr, bytes)                                                       \
+    do {                                                                         \
+        cudaError_t e_ = cudaMallocHost((void**)&(ptr), (bytes));                \
+        if (e_ != cudaSuccess) {                                                 \
+            free_all(m); delete m;                                               \
+            return fail(TNSIM_ENOMEM, std::string("cudaMallocHost: ") + cudaGetErrorString(e_)); \
+        }                                                                        \
+    } while (0)
+
+    ALLOC(m->d_sites, off);
+    ALLOC(m->d_chi, sizeof(int) * (n_qubits + 1));
+    ALLOC(m->d_ws, nG * 2 * m->ws_elems * m->esz);
+    ALLOC(m->d_s2, nG * 2 * m->capmax * sizeof(double));
+    ALLOC(m->d_perm, nG * 2 * m->capmax * sizeof(int));
+    ALLOC(m->d_spec, (size_t)(n_qubits + 1) * prm.chi_max * sizeof(double));
+    ALLOC(m->d_spec_k, sizeof(int) * (n_qubits + 1));
+    ALLOC(m->d_out, nG * sizeof(GateOut));
+    ALLOC(m->d_desc, nG * sizeof(GateDesc));
+    ALLOC(m->d_s1, (size_t)n_qubits * sizeof(Site1Desc));
+    ALLOC(m->d_gates, gate_doubles * sizeof(double));
+    ALLOC(m->d_sticky, sizeof(int));
+    ALLOC(m->d_stats, 8 * sizeof(unsigned long long));
+    HALLOC(m->h_out, nG * sizeof(GateOut));
+    HALLOC(m->h_chi, sizeof(int) * (n_qubits + 1));
+    for (auto& r : m->ring) {
+        HALLOC(r.desc, nG * sizeof(GateDesc));
+        HALLOC(r.s1, (size_t)n_qubits * sizeof(Site1Desc));
+        HALLOC(r.gates, gate_doubles * sizeof(double));
+        if (cudaEventCreateWithFlags(&r.done, cudaEventDisableTiming) != cudaSuccess) {
+            free_all(m); delete m;
+            return fail(TNSIM_ECUDA, "cudaEventCreate failed");
+        }
+    }
+#undef ALLOC
+#undef HALLOC
+    if (cuda_stream) {
+        m->stream = (cudaStream_t)cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&m->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            free_all(m); delete m;
+            return fail(TNSIM_ECUDA, "cudaStreamCreate failed");
+        }
+        m->own_stream = true;
+    }
+    // |0...0>: every site (1,2,1) = (1, 0)
+    std::vector<char> h0(m->esz * 2, 0);
+    if (dt == TNSIM_C64) { float one = 1.0f; std::memcpy(h0.data(), &one, 4); }
+    else { double one = 1.0; std::memcpy(h0.data(), &one, 8); }
+    std::vector<int> ones(n_qubits + 1, 1);
+    cudaError_t e = cudaSuccess;
+    for (int q = 0; q < n_qubits && e == cudaSuccess; ++q)
+        e = cudaMemcpy(m->d_sites + m->site_off[q], h0.data(), h0.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(m->d_chi, ones.data(), sizeof(int) * (n_qubits + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(m->d_spec_k, 0, sizeof(int) * (n_qubits + 1));
+    if (e == cudaSuccess) e = cudaMemset(m->d_sticky, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(m->d_stats, 0, 8 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(m->d_out, 0, nG * sizeof(GateOut));
+    if (e != cudaSuccess) {
+        free_all(m); delete m;
+        return fail(TNSIM_ECUDA, std::string("initialisation: ") + cudaGetErrorString(e));
+    }
+    *out = m;
+    return TNSIM_OK;
+}
+
+tnsim_status tnsim_mps_destroy(tnsim_mps* m) {
+    if (!m) return TNSIM_OK;
+    DevGuard g(m->device);
+    cudaStreamSynchronize(m->stream);
+    free_all(m);
+    delete m;
+    return TNSIM_OK;
+}
+
+tnsim_status tnsim_apply_layer_device(tnsim_mps* m, int32_t n2, const int32_t* q,
+                                      const double* g4x4_dev, const double* u1_dev, double* eps_dev) {
+    if (!m) return fail(TNSIM_EINVAL, "state is NULL");
+    DevGuard g(m->device);
+    tnsim_status s = check_pairs(m, n2, q);
+    if (s != TNSIM_OK) return s;
+    if (n2 > 0 && !g4x4_dev) return fail(TNSIM_EINVAL, "g4x4_dev is NULL");
+    Staging* stg = acquire_staging(m);
+    s = enqueue_layer(m, stg, n2, q, g4x4_dev, u1_dev, eps_dev);
+    CUDA_TRY(cudaEventRecord(stg->done, m->stream));
+    return s;
+}
+
+tnsim_status tnsim_apply_layer(tnsim_mps* m, int32_t n2, const int32_t* q, const double* g4x4,
+                               const double* u1, double* eps_out) {
+    if (!m) return fail(TNSIM_EINVAL, "state is NULL");
+    DevGuard g(m->device);
+    tnsim_status s = check_pairs(m, n2, q);
+    if (s != TNSIM_OK) return s;
+    if (n2 > 0 && !g4x4) return fail(TNSIM_EINVAL, "g4x4 is NULL");
+    if (n2 > 0 && !finite_all(g4x4, (size_t)n2 * 32)) return fail(TNSIM_EINVAL, "non-finite gate entry");
+    if (u1 && !finite_all(u1, (size_t)m->n * 8)) return fail(TNSIM_EINVAL, "non-finite one-qubit gate entry");
+    Staging* stg = acquire_staging(m);
+    double* dg = m->d_gates;
+    double* du = m->d_gates + (size_t)m->G * 32;
+    if (n2 > 0) std::memcpy(stg->gates, g4x4, sizeof(double) * 32 * n2);
+    if (u1) std::memcpy(stg->gates + (size_t)m->G * 32, u1, sizeof(double) * 8 * m->n);
+    if (n2 > 0) CUDA_TRY(cudaMemcpyAsync(dg, stg->gates, sizeof(double) * 32 * n2, cudaMemcpyHostToDevice, m->stream));
+    if (u1) CUDA_TRY(cudaMemcpyAsync(du, stg->gates + (size_t)m->G * 32, sizeof(double) * 8 * m->n,
+                                     cudaMemcpyHostToDevice, m->stream));
+    s = enqueue_layer(m, stg, n2, q, dg, u1 ? du : nullptr, nullptr);
+    CUDA_TRY(cudaEventRecord(stg->done, m->stream));
+    if (s != TNSIM_OK) return s;
+    if (n2 > 0) CUDA_TRY(cudaMemcpyAsync(m->h_out, m->d_out, sizeof(GateOut) * n2, cudaMemcpyDeviceToHost, m->stream));
+    s = refresh_dims(m);   // synchronises
+    if (s != TNSIM_OK) return s;
+    tnsim_status ret = TNSIM_OK;
+    for (int i = 0; i < n2; ++i) {
+        if (eps_out) eps_out[i] = m->h_out[i].eps;
+        if (m->h_out[i].status) ret = TNSIM_ENOCONV;
+    }
+    if (ret != TNSIM_OK) return fail(ret, "a Jacobi SVD reached max_sweeps (layer applied)");
+    return TNSIM_OK;
+}
+
+tnsim_status tnsim_apply_layers_batched(tnsim_mps* const* ms, int32_t n_circ, int32_t n_steps,
+                                        const int32_t* n2, const int32_t* const* q_ptrs,
+                                        const double* const* g_ptrs, const double* const* u1_ptrs) {
+    (void)ms; (void)n_circ; (void)n_steps; (void)n2; (void)q_ptrs; (void)g_ptrs; (void)u1_ptrs;
+    return fail(TNSIM_EUNSUPPORTED, "batched multi-state application is not built yet");
+}
+
+tnsim_status tnsim_sync(tnsim_mps* m) {
+    if (!m) return fail(TNSIM_EINVAL, "state is NULL");
+    DevGuard g(m->device);
+    tnsim_status s = refresh_dims(m);
+    if (s != TNSIM_OK) return s;
+    int sticky = 0;
+    CUDA_TRY(cudaMemcpy(&sticky, m->d_sticky, sizeof(int), cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemset(m->d_sticky, 0, sizeof(int)));
+    if (sticky) return fail(TNSIM_ENOCONV, "a Jacobi SVD reached max_sweeps (layer applied)");
+    return TNSIM_OK;
+}
+
+tnsim_status tnsim_bond_dims(tnsim_mps* m, int32_t* out) {
+    if (!m || !out) return fail(TNSIM_EINVAL, "NULL argument");
+    DevGuard g(m->device);
+    tnsim_status s = refresh_dims(m);
+    if (s != TNSIM_OK) return s;
+    for (int b = 0; b <= m->n; ++b) out[b] = m->ub[b];
+    return TNSIM_OK;
+}
+
+tnsim_status tnsim_bond_spectrum(tnsim_mps* m, int32_t bond, double* s_out, int32_t* k_out) {
+    if (!m || !s_out || !k_out) return fail(TNSIM_EINVAL, "NULL argument");
+    if (bond < 0 || bond > m->n) return fail(TNSIM_EINVAL, "bond out of range");
+    DevGuard g(m->device);
+    CUDA_TRY(cudaStreamSynchronize(m->stream));
+    int k = 0;
+    CUDA_TRY(cudaMemcpy(&k, m->d_spec_k + bond, sizeof(int), cudaMemcpyDeviceToHost));
+    *k_out = k;
+    if (k > 0) CUDA_TRY(cudaMemcpy(s_out, m->d_spec + (size_t)bond * m->p.chi_max, sizeof(double) * k,
+                                   cudaMemcpyDeviceToHost));
+    return TNSIM_OK;
+}
+
+tnsim_status tnsim_export_sites(tnsim_mps* m, double* out, int64_t cap, int64_t* needed) {
+    if (!m) return fail(TNSIM_EINVAL, "state is NULL");
+    DevGuard g(m->device);
+    tnsim_status s = refresh_dims(m);
+    if (s != TNSIM_OK) return s;
+    int64_t need = 0;
+    for (int q = 0; q < m->n; ++q) need += (int64_t)m->ub[q] * 2 * m->ub[q + 1] * 2;
+    if (needed) *needed = need;
+    if (!out) return TNSIM_OK;
+    if (cap < need) return fail(TNSIM_EINVAL, "export buffer too small");
+    std::vector<char> buf;
+    int64_t pos = 0;
+    for (int q = 0; q < m->n; ++q) {
+        const size_t cnt = (size_t)m->ub[q] * 2 * m->ub[q + 1];
+        buf.resize(cnt * m->esz);
+        CUDA_TRY(cudaMemcpy(buf.data(), site_ptr(m, q), cnt * m->esz, cudaMemcpyDeviceToHost));
+        if (m->dt == TNSIM_C64) {
+            const float* f = (const float*)buf.data();
+            for (size_t i = 0; i < 2 * cnt; ++i) out[pos + i] = (double)f[i];
+        } else {
+            std::memcpy(out + pos, buf.data(), cnt * 16);
+        }
+        pos += (int64_t)cnt * 2;
+    }
+    return TNSIM_OK;
+}
+
+tnsim_status tnsim_import_sites(tnsim_mps* m, const int32_t* dims, const double* data) {
+    if (!m || !dims || !data) return fail(TNSIM_EINVAL, "NULL argument");
+    if (dims[0] != 1 || dims[m->n] != 1) return fail(TNSIM_EINVAL, "terminal bonds must be 1");
+    for (int b = 1; b < m->n; ++b)
+        if (dims[b] < 1 || dims[b] > m->cap[b]) return fail(TNSIM_EINVAL, "bond dimension exceeds capacity");
+    DevGuard g(m->device);
+    CUDA_TRY(cudaStreamSynchronize(m->stream));
+    std::vector<char> buf;
+    int64_t pos = 0;
+    for (int q = 0; q < m->n; ++q) {
+        const size_t cnt = (size_t)dims[q] * 2 * dims[q + 1];
+        if (!finite_all(data + pos, 2 * cnt)) return fail(TNSIM_EINVAL, "non-finite site entry");
+        buf.resize(cnt * m->esz);
+        if (m->dt == TNSIM_C64) {
+            float* f = (float*)buf.data();
+            for (size_t i = 0; i < 2 * cnt; ++i) f[i] = (float)data[pos + i];
+        } else {
+            std::memcpy(buf.data(), data + pos, cnt * 16);
+        }
+        CUDA_TRY(cudaMemcpy(site_ptr(m, q), buf.data(), cnt * m->esz, cudaMemcpyHostToDevice));
+        pos += (int64_t)cnt * 2;
+    }
+    CUDA_TRY(cudaMemcpy(m->d_chi, dims, sizeof(int) * (m->n + 1), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemset(m->d_spec_k, 0, sizeof(int) * (m->n + 1)));
+    for (int b = 0; b <= m->n; ++b) m->ub[b] = dims[b];
+    return TNSIM_OK;
+}
+
+tnsim_status tnsim_amplitudes(tnsim_mps* m, int64_t n_str, const uint8_t* bits, double* amps_out) {
+    if (!m) return fail(TNSIM_EINVAL, "state is NULL");
+    if (n_str < 0) return fail(TNSIM_EINVAL, "n_str < 0");
+    if (n_str == 0) return TNSIM_OK;
+    if (!bits || !amps_out) return fail(TNSIM_EINVAL, "NULL argument");
+    DevGuard g(m->device);
+    tnsim_status s = refresh_dims(m);
+    if (s != TNSIM_OK) return s;
+    int chi_cap = 1;
+    for (int b = 0; b <= m->n; ++b) chi_cap = std::max(chi_cap, m->ub[b]);
+    const size_t nb = (size_t)n_str * m->n;
+    void** d_sites = nullptr;
+    uint8_t* d_bits = nullptr;
+    double* d_amps = nullptr;
+    std::vector<void*> ptrs(m->n);
+    for (int q = 0; q < m->n; ++q) ptrs[q] = site_ptr(m, q);
+    CUDA_TRY(cudaMalloc((void**)&d_sites, sizeof(void*) * m->n));
+    cudaError_t e = cudaMalloc((void**)&d_bits, nb);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d_amps, sizeof(double) * 2 * n_str);
+    if (e == cudaSuccess) e = cudaMemcpy(d_sites, ptrs.data(), sizeof(void*) * m->n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_bits, bits, nb, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = (m->dt == TNSIM_C64)
+                ? launch_amplitudes<float>(d_sites, m->d_chi, m->n, chi_cap, d_bits, n_str, d_amps, m->stream)
+                : launch_amplitudes<double>(d_sites, m->d_chi, m->n, chi_cap, d_bits, n_str, d_amps, m->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(amps_out, d_amps, sizeof(double) * 2 * n_str, cudaMemcpyDeviceToHost);
+    cudaFree(d_sites); cudaFree(d_bits); cudaFree(d_amps);
+    if (e != cudaSuccess) return fail(TNSIM_ECUDA, std::string("amplitudes: ") + cudaGetErrorString(e));
+    return TNSIM_OK;
+}
+
+tnsim_status tnsim_expect_pauli(tnsim_mps* m, int32_t n_terms, const char* paulis, double* out) {
+    if (!m) return fail(TNSIM_EINVAL, "state is NULL");
+    if (n_terms < 0) return fail(TNSIM_EINVAL, "n_terms < 0");
+    if (n_terms == 0) return TNSIM_OK;
+    if (!paulis || !out) return fail(TNSIM_EINVAL, "NULL argument");
+    const int n = m->n;
+    for (int64_t i = 0; i < (int64_t)n_terms * n; ++i) {
+        const char c = paulis[i];
+        if (c != 'I' && c != 'X' && c != 'Y' && c != 'Z') return fail(TNSIM_EINVAL, "Pauli characters must be I, X, Y, Z");
+    }
+    DevGuard g(m->device);
+    tnsim_status s = refresh_dims(m);
+    if (s != TNSIM_OK) return s;
+    int chi_cap = 1;
+    for (int b = 0; b <= n; ++b) chi_cap = std::max(chi_cap, m->ub[b]);
+    const size_t env = (size_t)chi_cap * chi_cap * m->esz;
+    // operators: I, X, Y, Z as 2x2 complex128
+    const double ops[4][8] = {{1, 0, 0, 0, 0, 0, 1, 0},
+                              {0, 0, 1, 0, 1, 0, 0, 0},
+                              {0, 0, 0, -1, 0, 1, 0, 0},
+                              {1, 0, 0, 0, 0, 0, -1, 0}};
+    char* d_L = nullptr; char* d_R = nullptr; char* d_tmp = nullptr; char* d_E = nullptr;
+    double* d_ops = nullptr; double* d_res = nullptr;
+    cudaError_t e = cudaMalloc((void**)&d_L, env * (n + 1));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d_R, env * (n + 1));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d_tmp, env * 2);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d_E, env * 2);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d_ops, sizeof(ops));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d_res, sizeof(double) * 2 * n_terms);
+    if (e == cudaSuccess) e = cudaMemcpy(d_ops, ops, sizeof(ops), cudaMemcpyHostToDevice);
+    // identity boundary environments: L_0 = [[1]], R_n = [[1]]
+    std::vector<char> one(m->esz, 0);
+    if (m->dt == TNSIM_C64) { float f = 1.0f; std::memcpy(one.data(), &f, 4); }
+    else { double f = 1.0; std::memcpy(one.data(), &f, 8); }
+    if (e == cudaSuccess) e = cudaMemcpy(d_L, one.data(), m->esz, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_R + env * n, one.data(), m->esz, cudaMemcpyHostToDevice);
+    auto transfer = [&](int q, int op, const char* ein, char* eout, int left) -> cudaError_t {
+        return (m->dt == TNSIM_C64)
+                   ? launch_transfer<float>(site_ptr(m, q), m->d_chi, q, d_ops + 8 * op, ein, d_tmp, eout,
+                                            chi_cap, left, m->stream)
+                   : launch_transfer<double>(site_ptr(m, q), m->d_chi, q, d_ops + 8 * op, ein, d_tmp, eout,
+                                             chi_cap, left, m->stream);
+    };
+    for (int q = 0; q < n && e == cudaSuccess; ++q) e = transfer(q, 0, d_L + env * q, d_L + env * (q + 1), 1);
+    for (int q = n - 1; q >= 0 && e == cudaSuccess; --q) e = transfer(q, 0, d_R + env * (q + 1), d_R + env * q, 0);
+    for (int t = 0; t < n_terms && e == cudaSuccess; ++t) {
+        const char* ps = paulis + (size_t)t * n;
+        int a = -1, b = -1;
+        for (int q = 0; q < n; ++q)
+            if (ps[q] != 'I') { if (a < 0) a = q; b = q; }
+        auto opi = [](char c) { return c == 'I' ? 0 : c == 'X' ? 1 : c == 'Y' ? 2 : 3; };
+        if (a < 0) {
+            e = (m->dt == TNSIM_C64) ? launch_close<float>(d_L + env * n, d_R + env * n, m->d_chi, n, d_res + 2 * t, m->stream)
+                                     : launch_close<double>(d_L + env * n, d_R + env * n, m->d_chi, n, d_res + 2 * t, m->stream);
+            continue;
+        }
+        const char* cur = d_L + env * a;
+        int pp = 0;
+        for (int q = a; q <= b && e == cudaSuccess; ++q) {
+            char* dst = d_E + env * pp;
+            e = transfer(q, opi(ps[q]), cur, dst, 1);
+            cur = dst;
+            pp ^= 1;
+        }
+        if (e == cudaSuccess)
+            e = (m->dt == TNSIM_C64) ? launch_close<float>(cur, d_R + env * (b + 1), m->d_chi, b + 1, d_res + 2 * t, m->stream)
+                                     : launch_close<double>(cur, d_R + env * (b + 1), m->d_chi, b + 1, d_res + 2 * t, m->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(out, d_res, sizeof(double) * 2 * n_terms, cudaMemcpyDeviceToHost);
+    cudaFree(d_L); cudaFree(d_R); cudaFree(d_tmp); cudaFree(d_E); cudaFree(d_ops); cudaFree(d_res);
+    if (e != cudaSuccess) return fail(TNSIM_ECUDA, std::string("expect_pauli: ") + cudaGetErrorString(e));
+    return TNSIM_OK;
+}
+
+tnsim_status tnsim_grad(const void*, const double*, int32_t, const void*, const tnsim_params*,
+                        double*, double*) {
+    return fail(TNSIM_EUNSUPPORTED, "tnsim_grad is not built yet");
+}
+
+tnsim_status tnsim_last_stats(tnsim_mps* m, tnsim_stats* out) {
+    if (!m || !out) return fail(TNSIM_EINVAL, "NULL argument");
+    DevGuard g(m->device);
+    CUDA_TRY(cudaStreamSynchronize(m->stream));
+    unsigned long long st[8];
+    CUDA_TRY(cudaMemcpy(st, m->d_stats, sizeof(st), cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemset(m->d_stats, 0, sizeof(st)));
+    out->gates = (int64_t)st[0];
+    out->sweeps = (int64_t)st[1];
+    out->rotations = (int64_t)st[2];
+    out->pair_visits = (int64_t)st[3];
+    out->visit_rows = (int64_t)st[4];
+    out->rotation_rows = (int64_t)st[5];
+    out->theta_cmacs = (int64_t)st[6];
+    out->right_cmacs = (int64_t)st[7];
+    return TNSIM_OK;
+}
+
+tnsim_status tnsim_profile_enable(tnsim_mps* m, int32_t on) {
+    if (!m) return fail(TNSIM_EINVAL, "state is NULL");
+    DevGuard g(m->device);
+    if (!on) {
+        CUDA_TRY(cudaStreamSynchronize(m->stream));
+        for (auto& r : m->recs) { m->ev_pool.push_back(r.a); m->ev_pool.push_back(r.b); }
+        m->recs.clear();
+    }
+    m->prof_on = on != 0;
+    return TNSIM_OK;
+}
+
+tnsim_status tnsim_profile_read(tnsim_mps* m, double* ms, int64_t* launches) {
+    if (!m || !ms || !launches) return fail(TNSIM_EINVAL, "NULL argument");
+    DevGuard g(m->device);
+    CUDA_TRY(cudaStreamSynchronize(m->stream));
+    for (int i = 0; i < TNSIM_K_COUNT; ++i) { ms[i] = 0.0; launches[i] = 0; }
+    for (auto& r : m->recs) {
+        float t = 0.f;
+        CUDA_TRY(cudaEventElapsedTime(&t, r.a, r.b));
+        ms[r.cls] += t;
+        launches[r.cls] += 1;
+        m->ev_pool.push_back(r.a);
+        m->ev_pool.push_back(r.b);
+    }
+    m->recs.clear();
+    return TNSIM_OK;
+}
+
+}  // extern "C"

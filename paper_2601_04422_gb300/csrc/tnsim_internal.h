@@ -1,0 +1,93 @@
+// Internal declarations shared by the kernels and the C-ABI host runtime.
+// Nothing here is part of the public ABI (include/tnsim.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace tnsim {
+
+// complex element type per arithmetic precision: interleaved (re, im)
+template <typename T> struct CT;
+template <> struct CT<float> { typedef float2 type; };
+template <> struct CT<double> { typedef double2 type; };
+
+// Results of one two-qubit update, written by the kernels (device memory).
+struct GateOut {
+    double frob2;                  // |theta|_F^2, accumulated by the theta kernel (FP64)
+    double eps;                    // relative discarded weight sum_{j>=k} s_j^2 / sum_j s_j^2
+    double scale;                  // renormalisation factor applied to the kept s
+    int k;                         // kept bond dimension
+    int sweeps;                    // Jacobi sweeps run (the last one rotated nothing if converged)
+    int status;                    // 0 ok, 4 = the Jacobi SVD reached its sweep cap
+    int rot_ctr[3];                // per-sweep rotation counters shared by a gate's cluster
+    unsigned long long rotations;  // column-pair rotations applied
+    unsigned long long visits;     // column pairs examined
+};
+
+// Everything a kernel needs about one gate (device memory, one per gate of a launch).
+// Bond dimensions are read from chi[] at run time, so a launch can be issued
+// before the previous layer's truncation ranks are known on the host.
+struct GateDesc {
+    void* siteA;          // slot of site q     (chi_q, 2, chi_{q+1}) row-major
+    void* siteB;          // slot of site q+1   (chi_{q+1}, 2, chi_{q+2}) row-major
+    int* chi;             // the state's bond dimensions chi_0..chi_n (device)
+    const double* g4;     // 4x4 complex128 gate, row-major interleaved
+    const double* uL;     // 2x2 complex128 applied to qubit q before g4, or null
+    const double* uR;     // 2x2 complex128 applied to qubit q+1 before g4, or null
+    void* theta0;         // (2chi_L) x (2chi_R) column-major copy of theta
+    void* W;              // (2chi_L) x (2chi_R) column-major Jacobi working matrix
+    double* s2;           // sorted squared column norms (length 2chi_R)
+    int* perm;            // column index of each sorted entry
+    double* spectrum;     // kept singular values of bond q+1 (chi_max doubles)
+    int* spec_k;          // kept count of bond q+1
+    double* eps_out;      // optional copy of the discarded weight (device), or null
+    GateOut* out;
+    int* sticky;          // the state's sticky status word (OR of gate statuses)
+    unsigned long long* stats;  // the state's 8 work counters (layout of tnsim_stats)
+    double cutoff;
+    int q;
+    int chi_max;
+    int renorm;
+    int pad_;
+};
+
+// One-qubit update of one site (Eq. 3).
+struct Site1Desc {
+    void* site;
+    const int* chi;
+    const double* u;      // 2x2 complex128
+    int q;
+    int pad_;
+};
+
+// Launch wrappers (each returns the launch error, if any).
+template <typename T>
+cudaError_t launch_theta(const GateDesc* d, int n_gates, int chiL_max, int chiR_max,
+                         cudaStream_t s);
+template <typename T>
+cudaError_t launch_jacobi(const GateDesc* d, int n_gates, int m_max, int n_max, double tol,
+                          int max_sweeps, cudaStream_t s);
+template <typename T>
+cudaError_t launch_truncate(const GateDesc* d, int n_gates, cudaStream_t s);
+template <typename T>
+cudaError_t launch_left(const GateDesc* d, int n_gates, int m_max, int k_max, cudaStream_t s);
+template <typename T>
+cudaError_t launch_right(const GateDesc* d, int n_gates, int k_max, int n_max, cudaStream_t s);
+template <typename T>
+cudaError_t launch_site1q(const Site1Desc* d, int n_sites, int cap_lr, cudaStream_t s);
+
+// read-out
+template <typename T>
+cudaError_t launch_amplitudes(void* const* sites, const int* chi, int n_qubits, int chi_cap,
+                              const uint8_t* bits, int64_t n_str, double* amps,
+                              cudaStream_t s);
+template <typename T>
+cudaError_t launch_transfer(const void* site, const int* chi, int q, const double* op,
+                            const void* e_in, void* tmp, void* e_out, int chi_cap,
+                            int from_left, cudaStream_t s);
+template <typename T>
+cudaError_t launch_close(const void* E, const void* Rt, const int* chi, int bond, double* out,
+                         cudaStream_t s);
+
+}  // namespace tnsim

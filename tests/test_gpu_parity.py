@@ -1,0 +1,316 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+The SVD gauge is not unique, so only gauge-invariant quantities are compared:
+amplitudes <x|psi> (phase included), per-bond singular values, discarded weights,
+bond dimensions, Pauli expectations and the state fidelity
+F = |<a|b>|^2 / (<a|a><b|b>).  Tolerances:
+  complex128 runs: 1e-10 relative;
+  complex64 runs: singular values within 1e-5 of s_max per bond (normwise) and
+  1 - F <= 1e-6; amplitude and expectation bounds are derived from F
+  (|a_gpu - a_ref| / |a_ref| <= 2 sqrt(1 - F) on a set of strings, which gives 2e-3).
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import dense
+from oracle import mps as om
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def T():
+    import __graft_entry__ as g
+    g.build()
+    import paper_2601_04422_gb300 as T
+    return T
+
+
+def _all_bits(n):
+    return np.array([[(x >> (n - 1 - i)) & 1 for i in range(n)] for x in range(2 ** n)], dtype=np.uint8)
+
+
+def _fidelity(sites_a, sites_b):
+    return om.fidelity(om.MPS(sites_a), om.MPS(sites_b))
+
+
+def _spectrum_err(m, ref, chi_max):
+    """max over bonds of max_j |s_gpu - s_ref| / s_max (zero-padded)."""
+    worst = 0.0
+    for b in range(1, ref.n):
+        sr = ref.spectrum[b]
+        sg = m.spectrum(b)
+        if sr is None:
+            assert len(sg) == 0
+            continue
+        k = max(len(sr), len(sg))
+        a = np.zeros(k); a[: len(sg)] = sg
+        c = np.zeros(k); c[: len(sr)] = sr
+        worst = max(worst, float(np.max(np.abs(a - c)) / sr[0]))
+    return worst
+
+
+# ----------------------------------------------------------------- complex128, exact
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3, 4, 5])
+def test_c1_complex128_exact(T, seed):
+    """10 qubits, depth 8, U(2) + SU(4), chi_max 32 (exact): every amplitude vs the dense vector."""
+    circ, p = W.config_c1(seed)
+    m = T.MPS(10, dtype=T.TNSIM_C128, chi_max=p["chi_max"])
+    eps = m.run(circ)
+    psi = dense.run_circuit(circ)
+    amps = m.amplitudes(_all_bits(10))
+    assert np.linalg.norm(amps - psi) / np.linalg.norm(psi) < 1e-10
+    ref, recs = om.run_circuit(circ, p["chi_max"])
+    assert list(m.bond_dims()) == ref.bond_dims()
+    assert _spectrum_err(m, ref, 32) < 1e-10
+    assert max(float(np.max(e)) for e in eps if len(e)) < 1e-20
+    m.close()
+
+
+def test_c1_complex64(T):
+    circ, p = W.config_c1(1)
+    m = T.MPS(10, dtype=T.TNSIM_C64, chi_max=p["chi_max"])
+    m.run(circ)
+    ref, _ = om.run_circuit(circ, p["chi_max"])
+    assert 1 - _fidelity(m.export_sites(), ref.sites) <= 1e-6
+    assert _spectrum_err(m, ref, 32) <= 1e-5
+    m.close()
+
+
+# ----------------------------------------------------------------- edge cases
+
+
+@pytest.mark.parametrize("n,chi,cutoff,depth", [
+    (2, 1, 0.0, 3), (2, 2, 0.0, 3), (3, 2, 0.0, 4), (5, 3, 0.0, 6), (12, 17, 0.0, 10),
+    (13, 33, 0.0, 12), (9, 64, 1e-3, 8), (11, 5, 1e-2, 7),
+])
+def test_edge_shapes_complex128(T, n, chi, cutoff, depth):
+    """Ragged and degenerate shapes: chi_max 1 (product state), odd widths, caps that are
+    not powers of two, a binding cutoff."""
+    circ = W.brickwork_u2_su4(n, depth, seed=n * 31 + chi)
+    m = T.MPS(n, dtype=T.TNSIM_C128, chi_max=chi, cutoff=cutoff)
+    eps = m.run(circ)
+    ref, recs = om.run_circuit(circ, chi, cutoff)
+    assert list(m.bond_dims()) == ref.bond_dims()
+    e_ref = np.array([r.eps for rr in recs for r in rr])
+    e_got = np.concatenate([e for e in eps if len(e)])
+    assert np.allclose(e_got, e_ref, rtol=1e-9, atol=1e-13)
+    assert _spectrum_err(m, ref, chi) < 1e-10
+    bits = W.random_bitstrings(n, 64, seed=n)
+    a_ref = om.amplitudes(ref, bits)
+    a_got = m.amplitudes(bits)
+    assert np.linalg.norm(a_got - a_ref) <= 1e-10 * max(np.linalg.norm(a_ref), 1e-300)
+    m.close()
+
+
+def test_empty_and_one_qubit_only_layers(T):
+    n = 7
+    m = T.MPS(n, dtype=T.TNSIM_C128, chi_max=8)
+    ref = om.zero_state(n)
+    rng = np.random.default_rng(5)
+    u1 = np.stack([W.haar_unitary(2, rng) for _ in range(n)])
+    lay0 = W.Layer(np.zeros(0, np.int32), np.zeros((0, 4, 4)), u1)
+    lay1 = W.Layer(np.array([1, 4], np.int32), np.stack([W.haar_su4(rng) for _ in range(2)]), u1)
+    lay2 = W.Layer(np.zeros(0, np.int32), np.zeros((0, 4, 4)), None)
+    for lay in (lay0, lay1, lay2, lay0):
+        before = list(m.bond_dims())
+        m.apply_layer(lay)
+        om.apply_layer(ref, lay, 8)
+        if lay.n2 == 0:
+            assert list(m.bond_dims()) == before
+    a = m.amplitudes(_all_bits(n))
+    assert np.linalg.norm(a - om.to_dense(ref)) < 1e-12
+    m.close()
+
+
+def test_identity_gate_keeps_state(T):
+    circ, p = W.config_c1(2)
+    m = T.MPS(10, dtype=T.TNSIM_C128, chi_max=32)
+    m.run(circ)
+    before = m.amplitudes(_all_bits(10))
+    eye = np.stack([np.eye(4, dtype=complex)] * 5)
+    m.apply_layer(W.Layer(np.arange(0, 10, 2, dtype=np.int32), eye))
+    after = m.amplitudes(_all_bits(10))
+    assert np.linalg.norm(after - before) < 1e-12
+    m.close()
+
+
+def test_gate_set_with_fused_one_qubit_gates(T):
+    """{H, CX, RZZ, RX} layers: one-qubit gates on paired qubits are fused into the 4x4
+    on the device, the others update their site; checked against the dense vector."""
+    circ = W.gateset_circuit(12, 14, seed=3)
+    m = T.MPS(12, dtype=T.TNSIM_C128, chi_max=64)
+    m.run(circ)
+    psi = dense.run_circuit(circ)
+    a = m.amplitudes(_all_bits(12))
+    assert np.linalg.norm(a - psi) / np.linalg.norm(psi) < 1e-10
+    m.close()
+
+
+def test_ghz_and_qft_closed_forms(T):
+    for n in (3, 8, 12):
+        m = T.MPS(n, dtype=T.TNSIM_C128, chi_max=16)
+        m.run(W.ghz_circuit(n))
+        a = m.amplitudes(np.array([[0] * n, [1] * n, [1] + [0] * (n - 1)], dtype=np.uint8))
+        assert np.allclose(a, [2 ** -0.5, 2 ** -0.5, 0], atol=1e-14)
+        assert max(m.bond_dims()) == 2
+        m.close()
+    n = 6
+    x = [1, 0, 1, 1, 0, 1]
+    m = T.MPS(n, dtype=T.TNSIM_C128, chi_max=64)
+    m.run(W.qft_nn_circuit(n, x))
+    a = m.amplitudes(_all_bits(n))
+    assert np.allclose(np.abs(a), 2 ** (-n / 2), atol=1e-13)
+    assert max(m.bond_dims()) == 1
+    m.close()
+
+
+# ----------------------------------------------------------------- schedules and variants
+
+
+def test_plain_schedule_matches_batched_bitwise(T):
+    circ = W.brickwork_su4(16, 10, seed=9)
+    out = []
+    for sched in (T.TNSIM_SCHED_BATCHED, T.TNSIM_SCHED_PLAIN):
+        m = T.MPS(16, dtype=T.TNSIM_C64, chi_max=32, schedule=sched)
+        m.run(circ)
+        out.append(m.export_sites())
+        m.close()
+    for a, b in zip(*out):
+        assert a.shape == b.shape and np.array_equal(a, b)
+
+
+def test_device_gate_variant_matches_host_variant(T):
+    torch = pytest.importorskip("torch")
+    circ = W.brickwork_u2_su4(14, 8, seed=4)
+    m1 = T.MPS(14, dtype=T.TNSIM_C64, chi_max=16)
+    m1.run(circ)
+    s = torch.cuda.Stream()
+    m2 = T.MPS(14, dtype=T.TNSIM_C64, chi_max=16, stream=s.cuda_stream)
+    eps_dev = torch.zeros(7, dtype=torch.float64, device="cuda")
+    for lay in circ.layers:
+        g = torch.from_numpy(np.ascontiguousarray(lay.g4).view(np.float64).copy()).cuda()
+        u = torch.from_numpy(np.ascontiguousarray(lay.u1).view(np.float64).copy()).cuda()
+        torch.cuda.synchronize()
+        T.tnsim_apply_layer_device(m2.h, lay.pairs, g.data_ptr(), u.data_ptr(), eps_dev.data_ptr())
+        m2.sync()
+    for a, b in zip(m1.export_sites(), m2.export_sites()):
+        assert np.array_equal(a, b)
+    m1.close(); m2.close()
+
+
+# ----------------------------------------------------------------- failures stay on the host
+
+
+def test_invalid_layers_are_rejected_without_touching_the_state(T):
+    circ, _ = W.config_c1(3)
+    m = T.MPS(10, dtype=T.TNSIM_C128, chi_max=32)
+    m.run(circ)
+    before = m.export_sites()
+    g = np.stack([W.haar_su4(np.random.default_rng(0))] * 2)
+    for q in ([0, 1], [8, 9], [-1, 3], [4, 4]):
+        with pytest.raises(T.TnsimError) as ei:
+            T.tnsim_apply_layer(m.h, np.array(q, np.int32), g)
+        assert ei.value.status == T.TNSIM_EINVAL
+    bad = g.copy()
+    bad[0, 0, 0] = np.nan
+    with pytest.raises(T.TnsimError):
+        T.tnsim_apply_layer(m.h, np.array([0, 4], np.int32), bad)
+    for a, b in zip(before, m.export_sites()):
+        assert np.array_equal(a, b)
+    m.close()
+
+
+def test_sweep_cap_reports_enoconv_and_keeps_going(T):
+    circ = W.brickwork_su4(12, 8, seed=2)
+    m = T.MPS(12, dtype=T.TNSIM_C64, chi_max=32, max_sweeps=1)
+    with pytest.warns(T.TnsimConvergenceWarning):
+        m.run(circ)
+    m2 = T.MPS(12, dtype=T.TNSIM_C64, chi_max=32)   # the context is still usable
+    m2.run(circ)
+    ref, _ = om.run_circuit(circ, 32)
+    assert 1 - _fidelity(m2.export_sites(), ref.sites) <= 1e-6
+    m.close(); m2.close()
+
+
+# ----------------------------------------------------------------- read-out
+
+
+def test_expect_pauli_matches_oracle(T):
+    circ, p = W.config_c1(4)
+    m = T.MPS(10, dtype=T.TNSIM_C128, chi_max=32)
+    m.run(circ)
+    ref, _ = om.run_circuit(circ, 32)
+    rng = np.random.default_rng(8)
+    terms = ["".join(rng.choice(list("IXYZ"), size=10)) for _ in range(10)]
+    terms += ["I" * 10, "Z" + "I" * 9, "I" * 9 + "X"]
+    terms += ["I" * i + "ZZ" + "I" * (8 - i) for i in range(9)]
+    got = m.expect_pauli(terms)
+    want = np.array([om.expect_pauli(ref, t) for t in terms])
+    assert np.max(np.abs(got - want)) < 1e-10
+    m.close()
+
+
+# ----------------------------------------------------------------- the 64-qubit chi 128 workload
+
+
+@pytest.mark.slow
+def test_c2_complex64_vs_oracle(T):
+    """64 qubits, depth 20 Haar SU(4) brickwork, chi_max 128, cutoff 1e-10, complex64
+    against the complex128 oracle: per-bond singular values, 1024 sampled amplitudes
+    (perfect sampling from the oracle state) plus 64 uniform strings, <Z_i Z_i+1>, F."""
+    circ, p = W.config_c2(1)
+    m = T.MPS(64, dtype=T.TNSIM_C64, chi_max=p["chi_max"], cutoff=p["cutoff"])
+    m.run(circ)
+    ref, _ = om.run_circuit(circ, p["chi_max"], p["cutoff"])
+    assert _spectrum_err(m, ref, 128) <= 1e-5
+    F = _fidelity(m.export_sites(), ref.sites)
+    assert 1 - F <= 1e-6
+    bits = np.concatenate([om.perfect_sample(ref, 1024, np.random.default_rng(1)),
+                           W.random_bitstrings(64, 64, seed=2)])
+    a_ref = om.amplitudes(ref, bits)
+    a_got = m.amplitudes(bits)
+    assert np.linalg.norm(a_got - a_ref) / np.linalg.norm(a_ref) <= 2e-3
+    zz = ["I" * i + "ZZ" + "I" * (62 - i) for i in range(63)]
+    got = m.expect_pauli(zz).real
+    want = np.array([om.expect_pauli(ref, t).real for t in zz]) / om.norm2(ref)
+    assert np.max(np.abs(got / om.norm2(om.MPS(m.export_sites())) - want)) <= 2e-3
+    m.close()
+
+
+# ----------------------------------------------------------------- full size, sampled gates
+
+
+@pytest.mark.slow
+def test_full_size_chi256_layer_sampled_gates(T):
+    """100 qubits, chi_max 256, Haar SU(4) brickwork, complex64, in the batched launch
+    configuration of the benchmark: after the bonds saturate, one more layer is
+    applied on the GPU; for sampled pairs the oracle applies the same gate to the
+    same (exported) input sites and the kept singular values, the discarded weight
+    and the gauge-invariant two-site block A'_q A'_{q+1} are compared."""
+    n, chi = 100, 256
+    circ = W.brickwork_su4(n, 12, seed=7)
+    m = T.MPS(n, dtype=T.TNSIM_C64, chi_max=chi)
+    for lay in circ.layers[:11]:
+        m.apply_layer(lay)
+    assert int(np.max(m.bond_dims())) == chi
+    before = m.export_sites()
+    last = circ.layers[11]
+    eps = m.apply_layer(last)
+    after = m.export_sites()
+    idx = [0, 3, len(last.pairs) // 2, len(last.pairs) - 1]
+    for i in idx:
+        q = int(last.pairs[i])
+        mm = om.MPS([before[q], before[q + 1]])
+        rec = om.apply_2q(mm, 0, last.g4[i], chi)
+        s_gpu = m.spectrum(q + 1)
+        assert len(s_gpu) == rec.k
+        assert np.max(np.abs(s_gpu - rec.s_kept)) / rec.s_kept[0] <= 1e-5
+        assert abs(eps[i] - rec.eps) <= 1e-5
+        blk_ref = np.einsum("lxb,byr->lxyr", mm.sites[0], mm.sites[1])
+        blk_gpu = np.einsum("lxb,byr->lxyr", after[q], after[q + 1])
+        assert np.linalg.norm(blk_gpu - blk_ref) / np.linalg.norm(blk_ref) <= 1e-4
+    m.close()
