@@ -11,8 +11,8 @@
 // If |g| > tol sqrt(a b):  zeta = (b - a) / (2|g|), t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)),
 // c = 1/sqrt(1+t^2), s = c t, and
 //     w_i <- c w_i - s e^{-i phi} w_j,     w_j <- s e^{i phi} w_i + c w_j,
-// which makes the pair orthogonal.  Columns whose norm is below eps*|theta|_F are
-// numerically zero and are not rotated.
+// which makes the pair orthogonal.  Columns whose norm is below
+// eps*sqrt(max(m,n))*|theta|_F are numerically zero and are not rotated.
 //
 // Schedule.  The columns are cut into blocks of BC.  A sweep visits every pair of
 // blocks once in round-robin ("circle") order; the P/2 block pairs of a round are
@@ -71,19 +71,26 @@ __device__ __forceinline__ int rotate_pair(C* __restrict__ xi, C* __restrict__ x
     const T gabs = sqrt(g2);
     const T zeta = (b - a) / (2 * gabs);
     const T t = copysign(T(1), zeta) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
-    const T c = T(1) / sqrt(T(1) + t * t);
-    const T s = c * t;
+    // c = 1/rr, s = t/rr with rr = sqrt(1 + t^2), and c - 1 = -t^2 / (rr (1 + rr)) formed
+    // directly.  Each new element is x + d, where the small correction d = (c-1) x + ...
+    // is summed first and then added to x with a single rounding.  Near convergence
+    // |(c-1) x| is below half an ulp of x: added to an already rounded x + ... it would
+    // always round away, leaving c = 1 and growing the pair's norm by a factor 1 + t^2
+    // per rotation (a systematic drift of the singular values in FP32).
+    const T rr = sqrt(T(1) + t * t);
+    const T cm1 = -(t * t) / (rr * (T(1) + rr));
+    const T s = t / rr;
     const T er = gr / gabs, ei = gi / gabs;
     const T sr = s * er, si = s * ei;     // s e^{i phi}
     for (int r = lane; r < m; r += 32) {
         const C u = xi[r], v = xj[r];
         C nu, nv;
-        // nu = c u - conj(s e) v
-        nu.x = fma(c, u.x, -fma(sr, v.x, si * v.y));
-        nu.y = fma(c, u.y, -fma(sr, v.y, -si * v.x));
-        // nv = (s e) u + c v
-        nv.x = fma(sr, u.x, fma(-si, u.y, c * v.x));
-        nv.y = fma(sr, u.y, fma(si, u.x, c * v.y));
+        // nu = c u - conj(s e) v = u + [(c-1) u - conj(s e) v]
+        nu.x = u.x + fma(-si, v.y, fma(-sr, v.x, cm1 * u.x));
+        nu.y = u.y + fma(si, v.x, fma(-sr, v.y, cm1 * u.y));
+        // nv = (s e) u + c v = v + [(c-1) v + (s e) u]
+        nv.x = v.x + fma(-si, u.y, fma(sr, u.x, cm1 * v.x));
+        nv.y = v.y + fma(si, u.x, fma(sr, u.y, cm1 * v.y));
         xi[r] = nu;
         xj[r] = nv;
     }
