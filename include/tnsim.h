@@ -192,6 +192,34 @@ tnsim_status tnsim_profile_enable(tnsim_mps* m, int32_t on);
  * have TNSIM_K_COUNT entries.  Synchronises, then resets.  Errors: EINVAL, ECUDA. */
 tnsim_status tnsim_profile_read(tnsim_mps* m, double* ms, int64_t* launches);
 
+/* One two-qubit update (merge, gate, truncated SVD, absorption; complex64) that
+ * allocates no memory.  The paper has no counterpart: it is for callers that cannot
+ * let a library call cudaMalloc -- a plugin inside an application whose memory pool
+ * owns the whole device, a process under a fixed device-memory budget, or a loop
+ * that must not synchronise the device (cudaMalloc/cudaFree may).
+ *   site_a  : device, complex64 (chi_l, 2, chi_m) row-major, overwritten by the new
+ *             left site (chi_l, 2, k); cap_a = its capacity in complex elements,
+ *             >= chi_l * 2 * max(chi_m, kmax) with kmax = min(chi_max, 2chi_l, 2chi_r);
+ *   site_b  : device, complex64 (chi_m, 2, chi_r), overwritten by the new right site
+ *             (k, 2, chi_r); cap_b >= max(chi_m, kmax) * 2 * chi_r;
+ *   g4x4    : host, the 4x4 complex128 gate (32 doubles); chi_max, cutoff and
+ *             renormalize as in tnsim_params;
+ *   cuda_stream : the cudaStream_t to run on (NULL = the legacy default stream);
+ *   k_out   : host, the kept bond dimension; eps_out (host, may be NULL) the
+ *             discarded weight; s_out (host, may be NULL, chi_max doubles) the kept
+ *             singular values.
+ * Limits: chi_l, chi_r <= 128 and chi_max <= 256 (EINVAL beyond).  Scratch is one
+ * fixed array of about 1.1 MB compiled into the library, held by every GPU that
+ * loads it until the process exits.  The first call on a device looks up that
+ * array's device address; make that first call before any stream capture.  All
+ * calls share the array, so calls whose work overlaps on the GPU race.  Synchronous.
+ * Errors: EINVAL, ENOCONV (the update was applied), ECUDA, EUNSUPPORTED. */
+tnsim_status tnsim_two_site_update_noalloc(void* site_a, int64_t cap_a, void* site_b,
+                                           int64_t cap_b, int32_t chi_l, int32_t chi_m,
+                                           int32_t chi_r, const double* g4x4, int32_t chi_max,
+                                           double cutoff, int32_t renormalize, void* cuda_stream,
+                                           int32_t* k_out, double* eps_out, double* s_out);
+
 /* Thread-local description of the last failure (empty string if none). */
 const char* tnsim_last_error(void);
 

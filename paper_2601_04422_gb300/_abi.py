@@ -84,6 +84,9 @@ TNSIM_K_NAMES = ["site1q", "theta", "jacobi", "truncate", "left", "right"]
 _sig("tnsim_last_stats", C.c_int, [_P, C.POINTER(tnsim_stats)])
 _sig("tnsim_profile_enable", C.c_int, [_P, C.c_int32])
 _sig("tnsim_profile_read", C.c_int, [_P, _DP, _I64P])
+_sig("tnsim_two_site_update_noalloc", C.c_int,
+     [_P, C.c_int64, _P, C.c_int64, C.c_int32, C.c_int32, C.c_int32, _DP, C.c_int32, C.c_double,
+      C.c_int32, _P, _I32P, _DP, _DP])
 _sig("tnsim_last_error", C.c_char_p, [])
 _sig("tnsim_version", C.c_char_p, [])
 
@@ -94,7 +97,8 @@ def exported_symbols():
             "tnsim_apply_layer_device", "tnsim_apply_layers_batched", "tnsim_sync",
             "tnsim_bond_dims", "tnsim_bond_spectrum", "tnsim_export_sites", "tnsim_import_sites",
             "tnsim_amplitudes", "tnsim_expect_pauli", "tnsim_grad", "tnsim_last_stats",
-            "tnsim_profile_enable", "tnsim_profile_read", "tnsim_last_error", "tnsim_version"]
+            "tnsim_profile_enable", "tnsim_profile_read", "tnsim_two_site_update_noalloc",
+            "tnsim_last_error", "tnsim_version"]
 
 
 def tnsim_last_error() -> str:
@@ -266,6 +270,22 @@ def tnsim_profile_read(h) -> dict:
     n = np.zeros(len(TNSIM_K_NAMES), dtype=np.int64)
     _check(lib.tnsim_profile_read(h, _dptr(ms), n.ctypes.data_as(_I64P)))
     return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(TNSIM_K_NAMES)}
+
+
+def tnsim_two_site_update_noalloc(site_a: int, cap_a: int, site_b: int, cap_b: int, chi_l: int,
+                                  chi_m: int, chi_r: int, g4x4, chi_max: int, cutoff: float = 0.0,
+                                  renormalize: bool = True, stream=None):
+    """One complex64 two-qubit update on caller-owned device buffers (raw pointers),
+    using the library's fixed scratch array.  Returns (k, eps, kept singular values)."""
+    g = np.ascontiguousarray(g4x4, dtype=np.complex128).reshape(4, 4).view(np.float64)
+    k = C.c_int32(0)
+    eps = C.c_double(0.0)
+    s = np.zeros(chi_max, dtype=np.float64)
+    _check(lib.tnsim_two_site_update_noalloc(_P(site_a), int(cap_a), _P(site_b), int(cap_b), int(chi_l),
+                                             int(chi_m), int(chi_r), _dptr(g), int(chi_max), float(cutoff),
+                                             int(bool(renormalize)), _P(int(stream)) if stream else None,
+                                             C.byref(k), C.byref(eps), _dptr(s)))
+    return k.value, eps.value, s[: k.value].copy()
 
 
 class MPS:

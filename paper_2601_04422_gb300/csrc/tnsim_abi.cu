@@ -53,6 +53,8 @@ struct Staging {
 
 }  // namespace
 
+void tnsim::set_last_error(const char* msg) { g_err = msg ? msg : ""; }
+
 struct tnsim_mps {
     int n = 0;
     tnsim_dtype dt = TNSIM_C64;

@@ -90,4 +90,7 @@ template <typename T>
 cudaError_t launch_close(const void* E, const void* Rt, const int* chi, int bond, double* out,
                          cudaStream_t s);
 
+// Set the thread-local message returned by tnsim_last_error().
+void set_last_error(const char* msg);
+
 }  // namespace tnsim
