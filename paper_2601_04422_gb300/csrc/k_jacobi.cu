@@ -1,4 +1,4 @@
-// Batched one-sided (Hestenes) Jacobi SVD of theta, one thread-block cluster per gate.
+// Batched one-sided (Hestenes) Jacobi SVD of theta for every gate of a launch.
 //
 // The paper decomposes theta with a Jacobi SVD (cusolverDnZgesvdj, Sec. III.B);
 // here the one-sided variant orthogonalises the n = 2chi_R columns of the
@@ -15,21 +15,23 @@
 // eps*sqrt(max(m,n))*|theta|_F are numerically zero and are not rotated.
 //
 // Schedule.  The columns are cut into blocks of BC.  A sweep visits every pair of
-// blocks once in round-robin ("circle") order; the P/2 block pairs of a round are
-// spread over the CTAs of the gate's cluster, and a cluster barrier separates
-// rounds (a block is touched by one CTA per round).  A visit stages both blocks in
-// shared memory, rotates the BC x BC cross pairs in BC rounds of BC disjoint pairs
-// (one warp per pair, lanes over rows, warp-shuffle reductions) and, in the first
-// round of a sweep, the pairs inside each block as well, then writes the blocks
-// back.  Each sweep therefore rotates every column pair exactly once.  A sweep that
-// rotates nothing ends the iteration; reaching max_sweeps sets status ENOCONV.
-// Every loop is bounded; the kernel never spins on memory.
-#include <cooperative_groups.h>
+// blocks once in round-robin ("circle") order: P - 1 rounds of P/2 disjoint block
+// pairs.  A visit stages both blocks in shared memory, rotates the BC x BC cross
+// pairs in BC rounds of BC disjoint pairs (one warp per pair, lanes over rows,
+// warp-shuffle reductions; each warp keeps its block-I column in registers) and, in
+// the first round of a sweep, the pairs inside each block as well, then writes the
+// blocks back.  Each sweep therefore rotates every column pair exactly once.  A sweep
+// that rotates nothing ends the gate's iteration; reaching max_sweeps sets ENOCONV.
+//
+// The launch is persistent: one CTA per SM (as occupancy allows) claims visits of
+// any gate from a device-side queue, so gates of different sizes and all rounds of
+// a layer share the machine without waves.  The visits of a round are independent;
+// a gate's next round opens when the last visit of the current one is reported.  An
+// idle CTA polls with a sleep; if nothing progresses for ~2^22 polls it sets an
+// error flag and leaves (the host reports ETIMEOUT).  No other wait exists.
 #include <float.h>
 
 #include "tnsim_internal.h"
-
-namespace cg = cooperative_groups;
 
 namespace tnsim {
 
@@ -97,6 +99,62 @@ __device__ __forceinline__ int rotate_pair(C* __restrict__ xi, C* __restrict__ x
     return 1;
 }
 
+// Rotation of a column pair whose first column lives in registers (xi[k] holds row
+// lane + 32 k) and whose second column lives in shared memory.  The second column is
+// read once, kept in registers for the update and written back once.
+template <typename T, typename C, int RPL>
+__device__ __forceinline__ int rotate_reg(C (&xi)[RPL], C* __restrict__ xjs, int m, int lane,
+                                          T tol2, T zthr) {
+    C xj[RPL];
+    T a = 0, b = 0, gr = 0, gi = 0;
+#pragma unroll
+    for (int k = 0; k < RPL; ++k) {
+        const int r = lane + 32 * k;
+        if (r < m) {
+            xj[k] = xjs[r];
+        } else {
+            xj[k].x = 0;
+            xj[k].y = 0;
+        }
+        const C u = xi[k], v = xj[k];
+        a = fma(u.x, u.x, fma(u.y, u.y, a));
+        b = fma(v.x, v.x, fma(v.y, v.y, b));
+        gr = fma(u.x, v.x, fma(u.y, v.y, gr));
+        gi = fma(u.x, v.y, fma(-u.y, v.x, gi));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+        gr += __shfl_xor_sync(0xffffffffu, gr, o);
+        gi += __shfl_xor_sync(0xffffffffu, gi, o);
+    }
+    const T g2 = gr * gr + gi * gi;
+    if (!(a > zthr && b > zthr && g2 / b > tol2 * a)) return 0;
+    const T gabs = sqrt(g2);
+    const T zeta = (b - a) / (2 * gabs);
+    const T t = copysign(T(1), zeta) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+    // same single-rounding update as rotate_pair
+    const T rr = sqrt(T(1) + t * t);
+    const T cm1 = -(t * t) / (rr * (T(1) + rr));
+    const T s = t / rr;
+    const T er = gr / gabs, ei = gi / gabs;
+    const T sr = s * er, si = s * ei;
+#pragma unroll
+    for (int k = 0; k < RPL; ++k) {
+        const int r = lane + 32 * k;
+        const C u = xi[k], v = xj[k];
+        C nu, nv;
+        nu.x = u.x + fma(-si, v.y, fma(-sr, v.x, cm1 * u.x));
+        nu.y = u.y + fma(si, v.x, fma(-sr, v.y, cm1 * u.y));
+        nv.x = v.x + fma(-si, u.y, fma(sr, u.x, cm1 * v.x));
+        nv.y = v.y + fma(si, u.x, fma(sr, u.y, cm1 * v.y));
+        xi[k] = nu;
+        if (r < m) xjs[r] = nv;
+    }
+    return 1;
+}
+
 template <typename C>
 __device__ __forceinline__ void copy_block_in(C* dst, const C* src, int count) {
     const int units = (int)((size_t)count * sizeof(C) / 16);
@@ -112,173 +170,282 @@ __device__ __forceinline__ void copy_block_out(C* dst, const C* src, int count) 
     for (int i = threadIdx.x; i < units; i += blockDim.x) __stcg(d + i, s[i]);
 }
 
-template <typename T, int BC>
-__global__ void __launch_bounds__(BC * 32, 1)
-k_jacobi(const GateDesc* __restrict__ gd, int CL, double tol_in, int max_sweeps) {
-    using C = typename CT<T>::type;
-    cg::cluster_group cluster = cg::this_cluster();
-    const int crank = (int)cluster.block_rank();
-    const int g = blockIdx.x / CL;
-    const GateDesc& d = gd[g];
-    const int chiL = d.chi[d.q], chiR = d.chi[d.q + 2];
-    const int m = 2 * chiL, n = 2 * chiR;
-    C* Wm = (C*)d.W;
-    GateOut* out = d.out;
+// Geometry of one gate's tournament: nb column blocks, P players (nb rounded up to
+// even), R rounds per sweep and V visits (block pairs) per round.
+struct Tour {
+    int m, n, nb, P, R, V;
+};
+template <int BC>
+__device__ __forceinline__ Tour tour_of(const GateDesc& d) {
+    Tour t;
+    t.m = 2 * d.chi[d.q];
+    t.n = 2 * d.chi[d.q + 2];
+    t.nb = (t.n + BC - 1) / BC;
+    t.P = t.nb + (t.nb & 1);
+    t.R = (t.nb == 1) ? 1 : t.P - 1;
+    t.V = (t.nb == 1) ? 1 : t.P / 2;
+    return t;
+}
 
+constexpr unsigned kSpinLimit = 1u << 22;   // idle polls without any progress before giving up
+constexpr int kScanTable = 2048;              // gates whose visit count is cached in shared memory
+
+// Persistent kernel: every CTA repeatedly claims one visit (gate g, global round
+// number, block pair v) from the gates' claim words, processes it, and reports it.
+// The last visit of a round advances that gate to its next round (and, at the end
+// of a sweep, decides convergence).  Gates are scanned in descriptor order, which
+// the host sorts by decreasing size.  A CTA never waits while holding a claim, so
+// a CTA with nothing to claim only waits for work that running CTAs are doing.
+template <typename T, int BC, int RPL>
+__global__ void __launch_bounds__(BC * 32, 1)
+k_jacobi(const GateDesc* __restrict__ gd, int n_gates, double tol_in, int max_sweeps,
+         JacobiCtl* __restrict__ ctl) {
+    using C = typename CT<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* X = reinterpret_cast<C*>(smem_raw);       // [2*BC][m], column-major
-    __shared__ int s_rot;
-    __shared__ unsigned long long s_vis;
+    __shared__ int s_g, s_rnd, s_v, s_exit, s_rot, s_vis;
+    __shared__ short s_V[kScanTable];            // visits per round of each gate
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nb = (n + BC - 1) / BC;
-    const int P = nb + (nb & 1);
-    // default tolerance sqrt(m) * eps (LAPACK's one-sided Jacobi uses the same scale),
-    // floored at 4 eps for tiny m; a column below eps*sqrt(max(m,n))*|theta|_F is zero
-    const double tol = tol_in > 0.0 ? tol_in : fmax(sqrt((double)m), 4.0) * Eps<T>::v;
-    const T tol2 = (T)(tol * tol);
-    const T zthr = (T)(Eps<T>::v * Eps<T>::v * (double)max(m, n) * out->frob2);
+    unsigned spins = 0, last_progress = 0;
+    for (int g = threadIdx.x; g < n_gates && g < kScanTable; g += blockDim.x)
+        s_V[g] = (short)tour_of<BC>(gd[g]).V;
+    __syncthreads();
 
-    if (crank == 0 && threadIdx.x == 0) {
-        out->rot_ctr[0] = 0;
-        out->rot_ctr[1] = 0;
-        out->rot_ctr[2] = 0;
-    }
-    if (threadIdx.x == 0) s_vis = 0;
-    __threadfence();
-    cluster.sync();
-
-    int sweep = 0;
-    bool converged = false;
-    unsigned long long total_rot = 0;
-    for (; sweep < max_sweeps; ++sweep) {
-        if (threadIdx.x == 0) s_rot = 0;
-        if (crank == 0 && threadIdx.x == 0) out->rot_ctr[(sweep + 1) % 3] = 0;
+    for (;;) {
+        if (warp == 0) {
+            // warp-parallel scan: each lane checks one gate per pass (one L2 round trip),
+            // the first claimable gate in descriptor order is tried with an atomic
+            int found = 0, fg = -1, frnd = 0, fv = 0;
+            for (int base = 0; base < n_gates && !found; base += 32) {
+                const int g = base + lane;
+                bool ok = false;
+                int V = 0;
+                GateOut* o = nullptr;
+                if (g < n_gates) {
+                    o = gd[g].out;
+                    V = g < kScanTable ? (int)s_V[g] : tour_of<BC>(gd[g]).V;
+                    const int fin = *((volatile int*)&o->finished);
+                    const unsigned long long cur = *((volatile unsigned long long*)&o->claim);
+                    ok = !fin && (unsigned)(cur & 0xffffffffull) < (unsigned)V;
+                }
+                unsigned mask = __ballot_sync(0xffffffffu, ok);
+                while (mask && !found) {
+                    const int l = __ffs(mask) - 1;
+                    int got = 0;
+                    if (lane == l) {
+                        const unsigned long long st = atomicAdd(&o->claim, 1ull);
+                        if ((unsigned)(st & 0xffffffffull) < (unsigned)V) {
+                            got = 1;
+                            fg = g;
+                            frnd = (int)(st >> 32);
+                            fv = (int)(st & 0xffffffffull);
+                        }
+                    }
+                    got = __shfl_sync(0xffffffffu, got, l);
+                    if (got) {
+                        fg = __shfl_sync(0xffffffffu, fg, l);
+                        frnd = __shfl_sync(0xffffffffu, frnd, l);
+                        fv = __shfl_sync(0xffffffffu, fv, l);
+                        found = 1;
+                    }
+                    mask &= mask - 1;
+                }
+            }
+            if (lane == 0) {
+                s_exit = 0;
+                s_g = found ? fg : -1;
+                s_rnd = frnd;
+                s_v = fv;
+                if (!found && (*((volatile int*)&ctl->n_finished) >= n_gates ||
+                               *((volatile int*)&ctl->error)))
+                    s_exit = 1;
+                s_rot = 0;
+                s_vis = 0;
+            }
+        }
         __syncthreads();
+        if (s_exit) break;
+        if (s_g < 0) {
+            if (threadIdx.x == 0) {
+                const unsigned p = *((volatile unsigned*)&ctl->progress);
+                if (p != last_progress) {
+                    last_progress = p;
+                    spins = 0;
+                } else if (++spins > kSpinLimit) {
+                    atomicExch(&ctl->error, 1);
+                }
+                __nanosleep(256);
+            }
+            __syncthreads();
+            continue;
+        }
+        __threadfence();   // order the claim before reading the blocks of the previous round
+
+        const int g = s_g, rnd = s_rnd, v = s_v;
+        const GateDesc& d = gd[g];
+        GateOut* out = d.out;
+        const Tour tg = tour_of<BC>(d);
+        const int m = tg.m, n = tg.n, nb = tg.nb, P = tg.P, R = tg.R;
+        const int sweep = rnd / R, round = rnd - sweep * R;
+        C* Wm = (C*)d.W;
+        // default tolerance sqrt(m) * eps (LAPACK's one-sided Jacobi uses the same scale),
+        // floored at 4 eps for tiny m; a column below eps*sqrt(max(m,n))*|theta|_F is zero
+        const double tol = tol_in > 0.0 ? tol_in : fmax(sqrt((double)m), 4.0) * Eps<T>::v;
+        const T tol2 = (T)(tol * tol);
+        const T zthr = (T)(Eps<T>::v * Eps<T>::v * (double)max(m, n) * out->frob2);
+
+        int I, J;
+        if (nb == 1) {
+            I = 0;
+            J = -1;
+        } else {
+            rr_pair(P, round, v, I, J);
+            if (I >= nb) { I = J; J = -1; }
+            else if (J >= nb) J = -1;
+            if (J >= 0 && J < I) { const int t = I; I = J; J = t; }
+        }
+        const bool intra = (round == 0);
         int my_rot = 0, my_vis = 0;
-        const int rounds = (nb == 1) ? 1 : P - 1;
-        for (int rnd = 0; rnd < rounds; ++rnd) {
-            const int pairs = (nb == 1) ? 1 : P / 2;
-            for (int v = crank; v < pairs; v += CL) {
-                int I, J;
-                if (nb == 1) { I = 0; J = -1; }
-                else {
-                    rr_pair(P, rnd, v, I, J);
-                    if (I >= nb) { I = J; J = -1; }
-                    else if (J >= nb) J = -1;
-                    if (J >= 0 && J < I) { int t = I; I = J; J = t; }
+        if (J >= 0 || intra) {
+            const int colI = I * BC, nI = min(BC, n - colI);
+            const int colJ = J >= 0 ? J * BC : 0, nJ = J >= 0 ? min(BC, n - colJ) : 0;
+            copy_block_in(X, Wm + (size_t)colI * m, nI * m);
+            if (J >= 0) copy_block_in(X + (size_t)BC * m, Wm + (size_t)colJ * m, nJ * m);
+            __syncthreads();
+            if (intra) {
+                // pairs inside block I (warps 0..BC/2-1) and inside block J (the rest)
+                for (int t = 0; t < BC - 1; ++t) {
+                    const int half = BC / 2;
+                    const int w = warp < half ? warp : warp - half;
+                    const int base = warp < half ? 0 : BC;
+                    const int nblk = warp < half ? nI : nJ;
+                    int a, b;
+                    rr_pair(BC, t, w, a, b);
+                    if (a < nblk && b < nblk) {
+                        my_vis += (lane == 0);
+                        my_rot += rotate_pair<T>(X + (size_t)(base + a) * m, X + (size_t)(base + b) * m,
+                                                 m, lane, tol2, zthr);
+                    }
+                    __syncthreads();
                 }
-                const bool intra = (rnd == 0);
-                if (J < 0 && !intra) continue;
-                const int colI = I * BC, nI = min(BC, n - colI);
-                const int colJ = J >= 0 ? J * BC : 0, nJ = J >= 0 ? min(BC, n - colJ) : 0;
-                copy_block_in(X, Wm + (size_t)colI * m, nI * m);
-                if (J >= 0) copy_block_in(X + (size_t)BC * m, Wm + (size_t)colJ * m, nJ * m);
-                __syncthreads();
-                if (intra) {
-                    // pairs inside block I (warps 0..BC/2-1) and inside block J (the rest)
-                    for (int t = 0; t < BC - 1; ++t) {
-                        const int half = BC / 2;
-                        const int w = warp < half ? warp : warp - half;
-                        const int base = warp < half ? 0 : BC;
-                        const int nblk = warp < half ? nI : nJ;
-                        int a, b;
-                        rr_pair(BC, t, w, a, b);
-                        if (a < nblk && b < nblk) {
-                            my_vis += (lane == 0);
-                            my_rot += rotate_pair<T>(X + (size_t)(base + a) * m,
-                                                     X + (size_t)(base + b) * m, m, lane, tol2, zthr);
-                        }
-                        __syncthreads();
+            }
+            if (J >= 0) {
+                // cross pairs: warp w keeps column I_w in registers and meets every
+                // column of J once, J_{(w + sft) mod BC} in round sft
+                C xi[RPL];
+                const C* ci = X + (size_t)warp * m;
+#pragma unroll
+                for (int k = 0; k < RPL; ++k) {
+                    const int r = lane + 32 * k;
+                    if (warp < nI && r < m) {
+                        xi[k] = ci[r];
+                    } else {
+                        xi[k].x = 0;
+                        xi[k].y = 0;
                     }
                 }
-                if (J >= 0) {
-                    for (int sft = 0; sft < BC; ++sft) {
-                        const int a = warp, b = (warp + sft) % BC;
-                        if (a < nI && b < nJ) {
-                            my_vis += (lane == 0);
-                            my_rot += rotate_pair<T>(X + (size_t)a * m, X + (size_t)(BC + b) * m, m,
-                                                     lane, tol2, zthr);
-                        }
-                        __syncthreads();
+                for (int sft = 0; sft < BC; ++sft) {
+                    const int b = (warp + sft) % BC;
+                    if (warp < nI && b < nJ) {
+                        my_vis += (lane == 0);
+                        my_rot += rotate_reg<T, C, RPL>(xi, X + (size_t)(BC + b) * m, m, lane, tol2, zthr);
                     }
+                    __syncthreads();
                 }
-                copy_block_out(Wm + (size_t)colI * m, X, nI * m);
-                if (J >= 0) copy_block_out(Wm + (size_t)colJ * m, X + (size_t)BC * m, nJ * m);
+                C* co = X + (size_t)warp * m;
+#pragma unroll
+                for (int k = 0; k < RPL; ++k) {
+                    const int r = lane + 32 * k;
+                    if (warp < nI && r < m) co[r] = xi[k];
+                }
                 __syncthreads();
             }
-            __threadfence();
-            cluster.sync();
+            copy_block_out(Wm + (size_t)colI * m, X, nI * m);
+            if (J >= 0) copy_block_out(Wm + (size_t)colJ * m, X + (size_t)BC * m, nJ * m);
         }
         if (lane == 0 && my_rot) atomicAdd(&s_rot, my_rot);
-        if (lane == 0 && my_vis) atomicAdd(&s_vis, (unsigned long long)my_vis);
+        if (lane == 0 && my_vis) atomicAdd(&s_vis, my_vis);
+        __threadfence();   // every thread's block stores before the report
         __syncthreads();
-        if (threadIdx.x == 0 && s_rot) atomicAdd(&out->rot_ctr[sweep % 3], s_rot);
-        total_rot += (threadIdx.x == 0) ? (unsigned long long)s_rot : 0ull;
-        __threadfence();
-        cluster.sync();
-        const int tot = *((volatile int*)&out->rot_ctr[sweep % 3]);
-        if (tot == 0) { converged = true; ++sweep; break; }
-    }
-    if (threadIdx.x == 0) {
-        if (total_rot) atomicAdd(&out->rotations, total_rot);
-        if (s_vis) atomicAdd(&out->visits, s_vis);
-        if (crank == 0) {
-            out->sweeps = sweep;
-            out->status = converged ? 0 : 4;
+        if (threadIdx.x == 0) {
+            if (s_rot) {
+                atomicAdd(&out->rot_sweep, s_rot);
+                atomicAdd(&out->rotations, (unsigned long long)s_rot);
+            }
+            if (s_vis) atomicAdd(&out->visits, (unsigned long long)s_vis);
+            __threadfence();
+            const int dn = atomicAdd(&out->done, 1) + 1;
+            if (dn == tg.V) {
+                // last visit of this round: advance the gate
+                out->done = 0;
+                bool fin = false;
+                if (round == R - 1) {
+                    const int rs = atomicExch(&out->rot_sweep, 0);
+                    if (rs == 0 || sweep + 1 >= max_sweeps) {
+                        fin = true;
+                        out->sweeps = sweep + 1;
+                        out->status = (rs == 0) ? 0 : 4;
+                    }
+                }
+                __threadfence();
+                if (fin) {
+                    atomicExch(&out->finished, 1);
+                    atomicAdd(&ctl->n_finished, 1);
+                } else {
+                    atomicExch(&out->claim, (unsigned long long)(rnd + 1) << 32);
+                }
+                atomicAdd(&ctl->progress, 1u);
+            }
         }
+        __syncthreads();
     }
 }
 
-template <typename T, int BC>
+template <typename T, int BC, int RPL>
 static cudaError_t launch_bc(const GateDesc* d, int n_gates, int m_max, int n_max, double tol,
-                             int max_sweeps, cudaStream_t s) {
+                             int max_sweeps, JacobiCtl* ctl, cudaStream_t s) {
     using C = typename CT<T>::type;
     const size_t smem = (size_t)2 * BC * m_max * sizeof(C);
-    cudaError_t e = cudaFuncSetAttribute(k_jacobi<T, BC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_jacobi<T, BC, RPL>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi<T, BC, RPL>, BC * 32, smem)) !=
+        cudaSuccess)
+        return e;
+    if (per_sm < 1) return cudaErrorLaunchOutOfResources;
+    // no more CTAs than visits that can run at once
     const int nb = (n_max + BC - 1) / BC;
-    const int pairs = (nb + (nb & 1)) / 2;
-    int CL = 1;
-    while (CL < 8 && CL < pairs) CL <<= 1;
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    for (;;) {
-        attr[0].val.clusterDim.x = CL;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.gridDim = dim3(n_gates * CL, 1, 1);
-        cfg.blockDim = dim3(BC * 32, 1, 1);
-        cfg.dynamicSmemBytes = smem;
-        cfg.stream = s;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        int max_clusters = 0;
-        e = cudaOccupancyMaxActiveClusters(&max_clusters, k_jacobi<T, BC>, &cfg);
-        if (e == cudaSuccess && max_clusters > 0) break;
-        (void)cudaGetLastError();
-        if (CL == 1) return e == cudaSuccess ? cudaErrorLaunchOutOfResources : e;
-        CL >>= 1;
-    }
-    return cudaLaunchKernelEx(&cfg, k_jacobi<T, BC>, d, CL, tol, max_sweeps);
+    const long long visits = (long long)n_gates * ((nb == 1) ? 1 : (nb + (nb & 1)) / 2);
+    long long grid = (long long)sms * per_sm;
+    if (grid > visits) grid = visits;
+    if (grid < 1) grid = 1;
+    k_jacobi<T, BC, RPL><<<(unsigned)grid, BC * 32, smem, s>>>(d, n_gates, tol, max_sweeps < 1 ? 1 : max_sweeps, ctl);
+    return cudaGetLastError();
 }
 
+// Block width BC and rows per lane RPL (= ceil(m_max / 32)) per precision: the two
+// staged blocks take 2 BC m_max elements of shared memory (at most 128 KB).
 template <typename T>
 cudaError_t launch_jacobi(const GateDesc* d, int n_gates, int m_max, int n_max, double tol,
-                          int max_sweeps, cudaStream_t s) {
-    using C = typename CT<T>::type;
+                          int max_sweeps, JacobiCtl* ctl, cudaStream_t s) {
     if (n_gates <= 0) return cudaSuccess;
-    const size_t budget = 200 * 1024;
-    if ((size_t)2 * 16 * m_max * sizeof(C) <= budget)
-        return launch_bc<T, 16>(d, n_gates, m_max, n_max, tol, max_sweeps, s);
-    if ((size_t)2 * 8 * m_max * sizeof(C) <= budget)
-        return launch_bc<T, 8>(d, n_gates, m_max, n_max, tol, max_sweeps, s);
-    return launch_bc<T, 4>(d, n_gates, m_max, n_max, tol, max_sweeps, s);
+    if (m_max <= 64) return launch_bc<T, 16, 2>(d, n_gates, m_max, n_max, tol, max_sweeps, ctl, s);
+    if (m_max <= 128) return launch_bc<T, 16, 4>(d, n_gates, m_max, n_max, tol, max_sweeps, ctl, s);
+    if (m_max <= 256) return launch_bc<T, 16, 8>(d, n_gates, m_max, n_max, tol, max_sweeps, ctl, s);
+    if constexpr (sizeof(T) == 4) {
+        if (m_max <= 512) return launch_bc<T, 16, 16>(d, n_gates, m_max, n_max, tol, max_sweeps, ctl, s);
+        return launch_bc<T, 8, 32>(d, n_gates, m_max, n_max, tol, max_sweeps, ctl, s);
+    } else {
+        if (m_max <= 512) return launch_bc<T, 8, 16>(d, n_gates, m_max, n_max, tol, max_sweeps, ctl, s);
+        return launch_bc<T, 4, 32>(d, n_gates, m_max, n_max, tol, max_sweeps, ctl, s);
+    }
 }
 
-template cudaError_t launch_jacobi<float>(const GateDesc*, int, int, int, double, int, cudaStream_t);
-template cudaError_t launch_jacobi<double>(const GateDesc*, int, int, int, double, int, cudaStream_t);
+template cudaError_t launch_jacobi<float>(const GateDesc*, int, int, int, double, int, JacobiCtl*, cudaStream_t);
+template cudaError_t launch_jacobi<double>(const GateDesc*, int, int, int, double, int, JacobiCtl*, cudaStream_t);
 
 }  // namespace tnsim

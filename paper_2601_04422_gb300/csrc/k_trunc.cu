@@ -117,7 +117,9 @@ __global__ void __launch_bounds__(TR_THREADS) k_truncate(const GateDesc* __restr
         if (d.eps_out) *d.eps_out = eps;
         d.chi[q + 1] = k;
         *d.spec_k = k;
-        if (out->status) atomicOr(d.sticky, out->status);
+        // a gate whose iteration never ended was abandoned by an idle-timeout (ETIMEOUT)
+        if (!out->finished) out->status = 5;
+        if (out->status) atomicMax(d.sticky, out->status);
         typedef unsigned long long u64;
         atomicAdd(&d.stats[0], 1ull);
         atomicAdd(&d.stats[1], (u64)out->sweeps);

@@ -80,6 +80,7 @@ struct tnsim_mps {
     double* d_gates = nullptr;     // G*32 + n*8
     int* d_sticky = nullptr;
     unsigned long long* d_stats = nullptr;   // 8 counters (tnsim_stats)
+    JacobiCtl* d_ctl = nullptr;    // control word of the persistent Jacobi launch
     GateOut* h_out = nullptr;      // pinned readback
     int* h_chi = nullptr;          // pinned readback
     Staging ring[kRing];
@@ -115,6 +116,7 @@ void free_all(tnsim_mps* m) {
     cudaFree(m->d_perm); cudaFree(m->d_spec); cudaFree(m->d_spec_k); cudaFree(m->d_out);
     cudaFree(m->d_desc); cudaFree(m->d_s1); cudaFree(m->d_gates); cudaFree(m->d_sticky);
     cudaFree(m->d_stats);
+    cudaFree(m->d_ctl);
     cudaFreeHost(m->h_out); cudaFreeHost(m->h_chi);
     for (auto& r : m->ring) {
         cudaFreeHost(r.desc); cudaFreeHost(r.s1); cudaFreeHost(r.gates);
@@ -253,8 +255,9 @@ tnsim_status launch_gates(cudaStream_t st, const std::vector<GateJob>& jobs, con
     cudaEvent_t ev = prof_begin(pm, st);
     CUDA_TRY(launch_theta<T>(d_desc, ng, chiL_max, chiR_max, st));
     prof_end(pm, st, TNSIM_K_THETA, ev);
+    CUDA_TRY(cudaMemsetAsync(pm->d_ctl, 0, sizeof(JacobiCtl), st));
     ev = prof_begin(pm, st);
-    CUDA_TRY(launch_jacobi<T>(d_desc, ng, m_max, n_max, tol, sweeps, st));
+    CUDA_TRY(launch_jacobi<T>(d_desc, ng, m_max, n_max, tol, sweeps, pm->d_ctl, st));
     prof_end(pm, st, TNSIM_K_JACOBI, ev);
     ev = prof_begin(pm, st);
     CUDA_TRY(launch_truncate<T>(d_desc, ng, st));
@@ -322,6 +325,12 @@ tnsim_status enqueue_layer(tnsim_mps* m, Staging* stg, int n2, const int32_t* q,
         jobs[i].uR = u1_dev ? u1_dev + (size_t)(q[i] + 1) * 8 : nullptr;
         jobs[i].eps_dev = eps_dev ? eps_dev + i : nullptr;
     }
+    // largest gates first: the persistent Jacobi kernel serves gates in this order
+    std::stable_sort(jobs.begin(), jobs.end(), [](const GateJob& a, const GateJob& b) {
+        const double ca = (double)a.m->ub[a.q] * a.m->ub[a.q + 2] * a.m->ub[a.q + 2];
+        const double cb = (double)b.m->ub[b.q] * b.m->ub[b.q + 2] * b.m->ub[b.q + 2];
+        return ca > cb;
+    });
     CUDA_TRY(cudaMemsetAsync(m->d_out, 0, sizeof(GateOut) * n2, st));
     const double tol = default_tol(m);
     const int sweeps = default_sweeps(m);
@@ -446,6 +455,7 @@ tnsim_status tnsim_mps_create(int32_t n_qubits, tnsim_dtype dt, const tnsim_para
     ALLOC(m->d_gates, gate_doubles * sizeof(double));
     ALLOC(m->d_sticky, sizeof(int));
     ALLOC(m->d_stats, 8 * sizeof(unsigned long long));
+    ALLOC(m->d_ctl, sizeof(JacobiCtl));
     HALLOC(m->h_out, nG * sizeof(GateOut));
     HALLOC(m->h_chi, sizeof(int) * (n_qubits + 1));
     for (auto& r : m->ring) {
@@ -534,12 +544,14 @@ tnsim_status tnsim_apply_layer(tnsim_mps* m, int32_t n2, const int32_t* q, const
     if (n2 > 0) CUDA_TRY(cudaMemcpyAsync(m->h_out, m->d_out, sizeof(GateOut) * n2, cudaMemcpyDeviceToHost, m->stream));
     s = refresh_dims(m);   // synchronises
     if (s != TNSIM_OK) return s;
-    tnsim_status ret = TNSIM_OK;
+    int worst = 0;
     for (int i = 0; i < n2; ++i) {
         if (eps_out) eps_out[i] = m->h_out[i].eps;
-        if (m->h_out[i].status) ret = TNSIM_ENOCONV;
+        worst = std::max(worst, m->h_out[i].status);
     }
-    if (ret != TNSIM_OK) return fail(ret, "a Jacobi SVD reached max_sweeps (layer applied)");
+    if (worst) CUDA_TRY(cudaMemset(m->d_sticky, 0, sizeof(int)));
+    if (worst == 5) return fail(TNSIM_ETIMEOUT, "the Jacobi kernel's idle CTAs saw no progress (layer incomplete)");
+    if (worst == 4) return fail(TNSIM_ENOCONV, "a Jacobi SVD reached max_sweeps (layer applied)");
     return TNSIM_OK;
 }
 
@@ -558,6 +570,7 @@ tnsim_status tnsim_sync(tnsim_mps* m) {
     int sticky = 0;
     CUDA_TRY(cudaMemcpy(&sticky, m->d_sticky, sizeof(int), cudaMemcpyDeviceToHost));
     CUDA_TRY(cudaMemset(m->d_sticky, 0, sizeof(int)));
+    if (sticky == 5) return fail(TNSIM_ETIMEOUT, "the Jacobi kernel's idle CTAs saw no progress (layer incomplete)");
     if (sticky) return fail(TNSIM_ENOCONV, "a Jacobi SVD reached max_sweeps (layer applied)");
     return TNSIM_OK;
 }

@@ -20,9 +20,20 @@ struct GateOut {
     int k;                         // kept bond dimension
     int sweeps;                    // Jacobi sweeps run (the last one rotated nothing if converged)
     int status;                    // 0 ok, 4 = the Jacobi SVD reached its sweep cap
-    int rot_ctr[3];                // per-sweep rotation counters shared by a gate's cluster
+    int finished;                  // the Jacobi iteration of this gate has ended
+    int done;                      // visits of the current round reported
+    int rot_sweep;                 // rotations of the current sweep
+    unsigned long long claim;      // (round << 32) | visits of that round claimed
     unsigned long long rotations;  // column-pair rotations applied
     unsigned long long visits;     // column pairs examined
+};
+
+// Control word of one persistent Jacobi launch (zeroed before the launch).
+struct JacobiCtl {
+    int n_finished;                // gates whose iteration has ended
+    int error;                     // set when idle CTAs saw no progress for too long
+    unsigned int progress;         // rounds completed, over all gates
+    int pad_;
 };
 
 // Everything a kernel needs about one gate (device memory, one per gate of a launch).
@@ -67,7 +78,7 @@ cudaError_t launch_theta(const GateDesc* d, int n_gates, int chiL_max, int chiR_
                          cudaStream_t s);
 template <typename T>
 cudaError_t launch_jacobi(const GateDesc* d, int n_gates, int m_max, int n_max, double tol,
-                          int max_sweeps, cudaStream_t s);
+                          int max_sweeps, JacobiCtl* ctl, cudaStream_t s);
 template <typename T>
 cudaError_t launch_truncate(const GateDesc* d, int n_gates, cudaStream_t s);
 template <typename T>

@@ -39,7 +39,8 @@ constexpr size_t OFF_OUT = al(OFF_DESC + sizeof(GateDesc));
 constexpr size_t OFF_CHI = al(OFF_OUT + sizeof(GateOut));              // 3 ints
 constexpr size_t OFF_SMALL = al(OFF_CHI + 4 * sizeof(int));            // spec_k, sticky
 constexpr size_t OFF_STATS = al(OFF_SMALL + 4 * sizeof(int));          // 8 u64
-constexpr size_t OFF_G4 = al(OFF_STATS + 8 * sizeof(unsigned long long));
+constexpr size_t OFF_CTL = al(OFF_STATS + 8 * sizeof(unsigned long long));
+constexpr size_t OFF_G4 = al(OFF_CTL + sizeof(JacobiCtl));
 constexpr size_t OFF_EPS = al(OFF_G4 + 32 * sizeof(double));
 constexpr size_t OFF_S2 = al(OFF_EPS + sizeof(double));
 constexpr size_t OFF_PERM = al(OFF_S2 + kNaMaxDim * sizeof(double));
@@ -138,9 +139,10 @@ extern "C" tnsim_status tnsim_two_site_update_noalloc(
     NA_TRY(cudaMemsetAsync(base + OFF_OUT, 0, sizeof(GateOut), st));
     NA_TRY(cudaMemsetAsync(base + OFF_SMALL, 0, 4 * sizeof(int), st));
     NA_TRY(cudaMemsetAsync(base + OFF_STATS, 0, 8 * sizeof(unsigned long long), st));
+    NA_TRY(cudaMemsetAsync(base + OFF_CTL, 0, sizeof(JacobiCtl), st));
     const GateDesc* dd = (const GateDesc*)(base + OFF_DESC);
     NA_TRY(launch_theta<float>(dd, 1, chi_l, chi_r, st));
-    NA_TRY(launch_jacobi<float>(dd, 1, 2 * chi_l, 2 * chi_r, 0.0, 40, st));
+    NA_TRY(launch_jacobi<float>(dd, 1, 2 * chi_l, 2 * chi_r, 0.0, 40, (JacobiCtl*)(base + OFF_CTL), st));
     NA_TRY(launch_truncate<float>(dd, 1, st));
     NA_TRY(launch_left<float>(dd, 1, 2 * chi_l, kcap, st));
     NA_TRY(launch_right<float>(dd, 1, kcap, 2 * chi_r, st));
@@ -151,6 +153,7 @@ extern "C" tnsim_status tnsim_two_site_update_noalloc(
     if (eps_out) *eps_out = o.eps;
     if (s_out) NA_TRY(cudaMemcpy(s_out, base + OFF_SPEC, sizeof(double) * o.k, cudaMemcpyDeviceToHost));
 #undef NA_TRY
+    if (o.status == 5) return na_fail(TNSIM_ETIMEOUT, "the Jacobi kernel saw no progress (update incomplete)");
     if (o.status) return na_fail(TNSIM_ENOCONV, "the Jacobi SVD reached its sweep cap (update applied)");
     return TNSIM_OK;
 }
