@@ -208,6 +208,9 @@ k_jacobi(const GateDesc* __restrict__ gd, int n_gates, double tol_in, int max_sw
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned spins = 0, last_progress = 0;
+    // where this CTA starts scanning: the front (largest gates) when the gates are few,
+    // a spread-out offset when they are many; afterwards the last gate it claimed
+    int scan0 = (n_gates > 2 * (int)gridDim.x) ? (int)(((long long)blockIdx.x * n_gates) / gridDim.x) & ~31 : 0;
     for (int g = threadIdx.x; g < n_gates && g < kScanTable; g += blockDim.x)
         s_V[g] = (short)tour_of<BC>(gd[g]).V;
     __syncthreads();
@@ -217,7 +220,10 @@ k_jacobi(const GateDesc* __restrict__ gd, int n_gates, double tol_in, int max_sw
             // warp-parallel scan: each lane checks one gate per pass (one L2 round trip),
             // the first claimable gate in descriptor order is tried with an atomic
             int found = 0, fg = -1, frnd = 0, fv = 0;
-            for (int base = 0; base < n_gates && !found; base += 32) {
+            const int nchunks = (n_gates + 31) / 32;
+            for (int c = 0; c < nchunks && !found; ++c) {
+                int base = scan0 + 32 * c;
+                if (base >= nchunks * 32) base -= nchunks * 32;
                 const int g = base + lane;
                 bool ok = false;
                 int V = 0;
@@ -252,6 +258,7 @@ k_jacobi(const GateDesc* __restrict__ gd, int n_gates, double tol_in, int max_sw
                     mask &= mask - 1;
                 }
             }
+            if (found) scan0 = fg & ~31;
             if (lane == 0) {
                 s_exit = 0;
                 s_g = found ? fg : -1;

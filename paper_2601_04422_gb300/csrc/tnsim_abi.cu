@@ -558,8 +558,155 @@ tnsim_status tnsim_apply_layer(tnsim_mps* m, int32_t n2, const int32_t* q, const
 tnsim_status tnsim_apply_layers_batched(tnsim_mps* const* ms, int32_t n_circ, int32_t n_steps,
                                         const int32_t* n2, const int32_t* const* q_ptrs,
                                         const double* const* g_ptrs, const double* const* u1_ptrs) {
-    (void)ms; (void)n_circ; (void)n_steps; (void)n2; (void)q_ptrs; (void)g_ptrs; (void)u1_ptrs;
-    return fail(TNSIM_EUNSUPPORTED, "batched multi-state application is not built yet");
+    if (n_circ < 0 || n_steps < 0) return fail(TNSIM_EINVAL, "negative count");
+    if (n_circ == 0 || n_steps == 0) return TNSIM_OK;
+    if (!ms || !n2 || !q_ptrs || !g_ptrs || !u1_ptrs) return fail(TNSIM_EINVAL, "NULL argument");
+    for (int i = 0; i < n_circ; ++i) {
+        if (!ms[i]) return fail(TNSIM_EINVAL, "state is NULL");
+        if (ms[i]->dt != ms[0]->dt) return fail(TNSIM_EINVAL, "all states must share the dtype");
+        if (ms[i]->device != ms[0]->device) return fail(TNSIM_EINVAL, "all states must be on one device");
+        for (int j = 0; j < i; ++j)
+            if (ms[j] == ms[i]) return fail(TNSIM_EINVAL, "a state appears twice");
+    }
+    // validate everything before launching anything
+    size_t max_gates = 0, max_u1 = 0, max_sites = 0;
+    for (int t = 0; t < n_steps; ++t) {
+        size_t ng = 0, nu = 0, ns = 0;
+        for (int i = 0; i < n_circ; ++i) {
+            const int k = t * n_circ + i;
+            tnsim_status s = check_pairs(ms[i], n2[k], q_ptrs[k]);
+            if (s != TNSIM_OK) return s;
+            if (n2[k] > 0 && !g_ptrs[k]) return fail(TNSIM_EINVAL, "gate pointer is NULL");
+            if (n2[k] > 0 && !finite_all(g_ptrs[k], (size_t)n2[k] * 32)) return fail(TNSIM_EINVAL, "non-finite gate entry");
+            if (u1_ptrs[k] && !finite_all(u1_ptrs[k], (size_t)ms[i]->n * 8))
+                return fail(TNSIM_EINVAL, "non-finite one-qubit gate entry");
+            ng += n2[k];
+            if (u1_ptrs[k]) { nu += ms[i]->n; ns += ms[i]->n; }
+        }
+        max_gates = std::max(max_gates, ng);
+        max_u1 = std::max(max_u1, nu);
+        max_sites = std::max(max_sites, ns);
+    }
+    tnsim_mps* m0 = ms[0];
+    DevGuard g(m0->device);
+    for (int i = 0; i < n_circ; ++i)
+        if (ms[i]->stream != m0->stream) CUDA_TRY(cudaStreamSynchronize(ms[i]->stream));
+    cudaStream_t st = m0->stream;
+
+    // per-call device buffers (stream-ordered allocator) and pinned staging
+    const size_t gate_doubles = max_gates * 32 + max_u1 * 8 + 1;
+    double* d_g = nullptr;
+    GateDesc* d_desc = nullptr;
+    GateOut* d_out = nullptr;
+    Site1Desc* d_s1 = nullptr;
+    double* h_g = nullptr;
+    GateDesc* h_desc = nullptr;
+    Site1Desc* h_s1 = nullptr;
+    GateOut* h_out = nullptr;
+    auto cleanup = [&]() {
+        cudaStreamSynchronize(st);
+        cudaFreeAsync(d_g, st); cudaFreeAsync(d_desc, st); cudaFreeAsync(d_out, st); cudaFreeAsync(d_s1, st);
+        cudaStreamSynchronize(st);
+        cudaFreeHost(h_g); cudaFreeHost(h_desc); cudaFreeHost(h_s1); cudaFreeHost(h_out);
+    };
+    cudaError_t e = cudaMallocAsync((void**)&d_g, sizeof(double) * gate_doubles, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&d_desc, sizeof(GateDesc) * (max_gates + 1), st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&d_out, sizeof(GateOut) * (max_gates + 1), st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&d_s1, sizeof(Site1Desc) * (max_sites + 1), st);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&h_g, sizeof(double) * gate_doubles);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&h_desc, sizeof(GateDesc) * (max_gates + 1));
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&h_s1, sizeof(Site1Desc) * (max_sites + 1));
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&h_out, sizeof(GateOut) * (max_gates + 1));
+    if (e != cudaSuccess) {
+        cleanup();
+        return fail(TNSIM_ENOMEM, std::string("batched buffers: ") + cudaGetErrorString(e));
+    }
+    const double tol = m0->p.jacobi_tol;
+    int sweeps = 0;
+    for (int i = 0; i < n_circ; ++i) sweeps = std::max(sweeps, default_sweeps(ms[i]));
+    int worst = 0;
+    tnsim_status ret = TNSIM_OK;
+    for (int t = 0; t < n_steps && ret == TNSIM_OK; ++t) {
+        // stage this step's gates and one-qubit gates
+        size_t gpos = 0, upos = max_gates * 32;
+        std::vector<GateJob> jobs;
+        int ns = 0, caplr = 1;
+        for (int i = 0; i < n_circ; ++i) {
+            const int k = t * n_circ + i;
+            tnsim_mps* m = ms[i];
+            const double* u_dev = nullptr;
+            if (u1_ptrs[k]) {
+                std::memcpy(h_g + upos, u1_ptrs[k], sizeof(double) * 8 * m->n);
+                u_dev = d_g + upos;
+                upos += (size_t)m->n * 8;
+                std::vector<char> used(m->n, 0);
+                for (int j = 0; j < n2[k]; ++j) used[q_ptrs[k][j]] = used[q_ptrs[k][j] + 1] = 1;
+                for (int sidx = 0; sidx < m->n; ++sidx) {
+                    if (used[sidx]) continue;
+                    Site1Desc& d = h_s1[ns++];
+                    d.site = site_ptr(m, sidx);
+                    d.chi = m->d_chi;
+                    d.u = u_dev + (size_t)sidx * 8;
+                    d.q = sidx;
+                    d.pad_ = 0;
+                    caplr = std::max(caplr, m->ub[sidx] * m->ub[sidx + 1]);
+                }
+            }
+            if (n2[k] > 0) std::memcpy(h_g + gpos, g_ptrs[k], sizeof(double) * 32 * n2[k]);
+            for (int j = 0; j < n2[k]; ++j) {
+                GateJob jb;
+                jb.m = m;
+                jb.q = q_ptrs[k][j];
+                jb.slot = j;
+                jb.g4 = d_g + gpos + (size_t)j * 32;
+                jb.uL = u_dev ? u_dev + (size_t)jb.q * 8 : nullptr;
+                jb.uR = u_dev ? u_dev + (size_t)(jb.q + 1) * 8 : nullptr;
+                jb.eps_dev = nullptr;
+                jobs.push_back(jb);
+            }
+            gpos += (size_t)n2[k] * 32;
+        }
+        e = cudaMemcpyAsync(d_g, h_g, sizeof(double) * gate_doubles, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && ns > 0) e = cudaMemcpyAsync(d_s1, h_s1, sizeof(Site1Desc) * ns, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) { ret = fail(TNSIM_ECUDA, cudaGetErrorString(e)); break; }
+        if (ns > 0) {
+            cudaEvent_t ev = prof_begin(m0, st);
+            e = (m0->dt == TNSIM_C64) ? launch_site1q<float>(d_s1, ns, caplr, st) : launch_site1q<double>(d_s1, ns, caplr, st);
+            prof_end(m0, st, TNSIM_K_SITE1Q, ev);
+            if (e != cudaSuccess) { ret = fail(TNSIM_ECUDA, cudaGetErrorString(e)); break; }
+        }
+        if (!jobs.empty()) {
+            std::stable_sort(jobs.begin(), jobs.end(), [](const GateJob& a, const GateJob& b) {
+                const double ca = (double)a.m->ub[a.q] * a.m->ub[a.q + 2] * a.m->ub[a.q + 2];
+                const double cb = (double)b.m->ub[b.q] * b.m->ub[b.q + 2] * b.m->ub[b.q + 2];
+                return ca > cb;
+            });
+            e = cudaMemsetAsync(d_out, 0, sizeof(GateOut) * jobs.size(), st);
+            if (e != cudaSuccess) { ret = fail(TNSIM_ECUDA, cudaGetErrorString(e)); break; }
+            ret = upload_desc(st, jobs, h_desc, d_desc, d_out);
+            if (ret != TNSIM_OK) break;
+            ret = launch_gates_dt(m0->dt, st, jobs, d_desc, tol, sweeps);
+            if (ret != TNSIM_OK) break;
+            // the pinned staging is reused by the next step
+            e = cudaMemcpyAsync(h_out, d_out, sizeof(GateOut) * jobs.size(), cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) { ret = fail(TNSIM_ECUDA, cudaGetErrorString(e)); break; }
+            for (size_t j = 0; j < jobs.size(); ++j) worst = std::max(worst, h_out[j].status);
+        } else {
+            e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) { ret = fail(TNSIM_ECUDA, cudaGetErrorString(e)); break; }
+        }
+    }
+    cleanup();
+    if (ret != TNSIM_OK) return ret;
+    for (int i = 0; i < n_circ; ++i) {
+        tnsim_status s = refresh_dims(ms[i]);
+        if (s != TNSIM_OK) return s;
+        CUDA_TRY(cudaMemsetAsync(ms[i]->d_sticky, 0, sizeof(int), ms[i]->stream));
+    }
+    if (worst == 5) return fail(TNSIM_ETIMEOUT, "the Jacobi kernel's idle CTAs saw no progress (step incomplete)");
+    if (worst == 4) return fail(TNSIM_ENOCONV, "a Jacobi SVD reached max_sweeps (steps applied)");
+    return TNSIM_OK;
 }
 
 tnsim_status tnsim_sync(tnsim_mps* m) {

@@ -237,6 +237,75 @@ def test_sweep_cap_reports_enoconv_and_keeps_going(T):
     m.close(); m2.close()
 
 
+# ----------------------------------------------------------------- many states in one launch
+
+
+def _steps_of(circs):
+    depth = max(len(c.layers) for c in circs)
+    steps = []
+    for t in range(depth):
+        row = []
+        for c in circs:
+            if t < len(c.layers):
+                l = c.layers[t]
+                row.append((l.pairs, l.g4, l.u1))
+            else:
+                row.append(None)
+        steps.append(row)
+    return steps
+
+
+def test_batched_states_match_oracle_complex128(T):
+    """Six circuits of uneven width, depth and chi_max, every step of every circuit in
+    the same launches, against the oracle run circuit by circuit."""
+    spec = [(8, 4, 4, 1), (12, 7, 8, 2), (16, 10, 16, 3), (20, 6, 32, 4), (10, 9, 8, 5), (14, 8, 16, 6)]
+    circs = [W.brickwork_u2_su4(n, d, seed=s) for n, d, _, s in spec]
+    ms = [T.MPS(n, dtype=T.TNSIM_C128, chi_max=chi) for n, _, chi, _ in spec]
+    T.tnsim_apply_layers_batched([m.h for m in ms], _steps_of(circs))
+    for (n, d, chi, _), c, m in zip(spec, circs, ms):
+        ref, _ = om.run_circuit(c, chi)
+        assert list(m.bond_dims()) == ref.bond_dims()
+        assert _spectrum_err(m, ref, chi) < 1e-10
+        bits = W.random_bitstrings(n, 64, seed=n)
+        a_ref = om.amplitudes(ref, bits)
+        assert np.linalg.norm(m.amplitudes(bits) - a_ref) <= 1e-10 * np.linalg.norm(a_ref)
+        m.close()
+
+
+@pytest.mark.slow
+def test_c4_batch_256_circuits(T):
+    """256 independent Haar SU(4) brickwork circuits (width U{16..128}, depth U{8..32},
+    chi_max in {16..256}), complex64, all in one batched call for all but the last
+    step; the last step runs as one more batched call and is checked, for a sample of
+    circuits, against the oracle applied to the same (exported) input states."""
+    batch = W.batch_circuits(256, base_seed=1000)
+    circs = [c for c, _ in batch]
+    ms = [T.MPS(c.n_qubits, dtype=T.TNSIM_C64, chi_max=chi) for c, chi in batch]
+    steps = _steps_of(circs)
+    T.tnsim_apply_layers_batched([m.h for m in ms], steps[:-1])
+    last = len(steps) - 1
+    sample = [i for i, c in enumerate(circs) if len(c.layers) == len(steps)][:3]
+    sample += [int(np.argmax([chi for _, chi in batch]))]
+    before = {i: ms[i].export_sites() for i in sample}
+    T.tnsim_apply_layers_batched([m.h for m in ms], steps[last:])
+    for i in sample:
+        c, chi = batch[i]
+        if len(c.layers) <= last:
+            continue
+        lay = c.layers[last]
+        ref = om.MPS(before[i])
+        recs = om.apply_layer(ref, lay, chi)
+        for r in recs:
+            sg = ms[i].spectrum(r.q + 1)
+            k = max(len(sg), r.k)
+            a = np.zeros(k); a[: len(sg)] = sg
+            b = np.zeros(k); b[: r.k] = r.s_kept
+            assert np.max(np.abs(a - b)) / r.s_kept[0] <= 1e-5
+        assert 1 - om.fidelity(om.MPS(ms[i].export_sites()), ref) <= 1e-6
+    for m in ms:
+        m.close()
+
+
 # ----------------------------------------------------------------- read-out
 
 
