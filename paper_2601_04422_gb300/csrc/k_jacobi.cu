@@ -99,28 +99,43 @@ __device__ __forceinline__ int rotate_pair(C* __restrict__ xi, C* __restrict__ x
     return 1;
 }
 
-// Rotation of a column pair whose first column lives in registers (xi[k] holds row
-// lane + 32 k) and whose second column lives in shared memory.  The second column is
-// read once, kept in registers for the update and written back once.
-template <typename T, typename C, int RPL>
+// Rows owned by a lane in the register-resident layout: element k of a lane is row
+// 64 (k / 2) + 2 lane + (k % 2), so each lane moves two consecutive rows with one
+// 16-byte shared-memory access.
+__device__ __forceinline__ int reg_row(int lane, int k) { return 64 * (k >> 1) + 2 * lane + (k & 1); }
+
+// Rotation of a column pair whose first column lives in registers (layout above) and
+// whose second column lives in shared memory.  The second column is read once, kept
+// in registers for the update and written back once.  FULL: m == 32 * RPL, so no row
+// needs a bounds test.
+template <typename T, typename C, int RPL, bool FULL>
 __device__ __forceinline__ int rotate_reg(C (&xi)[RPL], C* __restrict__ xjs, int m, int lane,
                                           T tol2, T zthr) {
     C xj[RPL];
     T a = 0, b = 0, gr = 0, gi = 0;
 #pragma unroll
-    for (int k = 0; k < RPL; ++k) {
-        const int r = lane + 32 * k;
-        if (r < m) {
-            xj[k] = xjs[r];
+    for (int k = 0; k < RPL; k += 2) {
+        const int r = reg_row(lane, k);
+        if (FULL || r < m) {
+            // r and m are even: rows r and r + 1 are both present
+            if constexpr (sizeof(C) == 8) {
+                const float4 v = *reinterpret_cast<const float4*>(xjs + r);
+                xj[k].x = v.x; xj[k].y = v.y; xj[k + 1].x = v.z; xj[k + 1].y = v.w;
+            } else {
+                xj[k] = xjs[r];
+                xj[k + 1] = xjs[r + 1];
+            }
         } else {
-            xj[k].x = 0;
-            xj[k].y = 0;
+            xj[k].x = 0; xj[k].y = 0; xj[k + 1].x = 0; xj[k + 1].y = 0;
         }
-        const C u = xi[k], v = xj[k];
-        a = fma(u.x, u.x, fma(u.y, u.y, a));
-        b = fma(v.x, v.x, fma(v.y, v.y, b));
-        gr = fma(u.x, v.x, fma(u.y, v.y, gr));
-        gi = fma(u.x, v.y, fma(-u.y, v.x, gi));
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const C u = xi[k + e], v = xj[k + e];
+            a = fma(u.x, u.x, fma(u.y, u.y, a));
+            b = fma(v.x, v.x, fma(v.y, v.y, b));
+            gr = fma(u.x, v.x, fma(u.y, v.y, gr));
+            gi = fma(u.x, v.y, fma(-u.y, v.x, gi));
+        }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -141,16 +156,27 @@ __device__ __forceinline__ int rotate_reg(C (&xi)[RPL], C* __restrict__ xjs, int
     const T er = gr / gabs, ei = gi / gabs;
     const T sr = s * er, si = s * ei;
 #pragma unroll
-    for (int k = 0; k < RPL; ++k) {
-        const int r = lane + 32 * k;
-        const C u = xi[k], v = xj[k];
-        C nu, nv;
-        nu.x = u.x + fma(-si, v.y, fma(-sr, v.x, cm1 * u.x));
-        nu.y = u.y + fma(si, v.x, fma(-sr, v.y, cm1 * u.y));
-        nv.x = v.x + fma(-si, u.y, fma(sr, u.x, cm1 * v.x));
-        nv.y = v.y + fma(si, u.x, fma(sr, u.y, cm1 * v.y));
-        xi[k] = nu;
-        if (r < m) xjs[r] = nv;
+    for (int k = 0; k < RPL; k += 2) {
+        const int r = reg_row(lane, k);
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const C u = xi[k + e], v = xj[k + e];
+            C nu, nv;
+            nu.x = u.x + fma(-si, v.y, fma(-sr, v.x, cm1 * u.x));
+            nu.y = u.y + fma(si, v.x, fma(-sr, v.y, cm1 * u.y));
+            nv.x = v.x + fma(-si, u.y, fma(sr, u.x, cm1 * v.x));
+            nv.y = v.y + fma(si, u.x, fma(sr, u.y, cm1 * v.y));
+            xi[k + e] = nu;
+            xj[k + e] = nv;
+        }
+        if (FULL || r < m) {
+            if constexpr (sizeof(C) == 8) {
+                *reinterpret_cast<float4*>(xjs + r) = make_float4(xj[k].x, xj[k].y, xj[k + 1].x, xj[k + 1].y);
+            } else {
+                xjs[r] = xj[k];
+                xjs[r + 1] = xj[k + 1];
+            }
+        }
     }
     return 1;
 }
@@ -344,7 +370,7 @@ k_jacobi(const GateDesc* __restrict__ gd, int n_gates, double tol_in, int max_sw
                 const C* ci = X + (size_t)warp * m;
 #pragma unroll
                 for (int k = 0; k < RPL; ++k) {
-                    const int r = lane + 32 * k;
+                    const int r = reg_row(lane, k);
                     if (warp < nI && r < m) {
                         xi[k] = ci[r];
                     } else {
@@ -352,18 +378,21 @@ k_jacobi(const GateDesc* __restrict__ gd, int n_gates, double tol_in, int max_sw
                         xi[k].y = 0;
                     }
                 }
+                const bool full = (m == 32 * RPL);
                 for (int sft = 0; sft < BC; ++sft) {
                     const int b = (warp + sft) % BC;
                     if (warp < nI && b < nJ) {
                         my_vis += (lane == 0);
-                        my_rot += rotate_reg<T, C, RPL>(xi, X + (size_t)(BC + b) * m, m, lane, tol2, zthr);
+                        C* xjs = X + (size_t)(BC + b) * m;
+                        my_rot += full ? rotate_reg<T, C, RPL, true>(xi, xjs, m, lane, tol2, zthr)
+                                       : rotate_reg<T, C, RPL, false>(xi, xjs, m, lane, tol2, zthr);
                     }
                     __syncthreads();
                 }
                 C* co = X + (size_t)warp * m;
 #pragma unroll
                 for (int k = 0; k < RPL; ++k) {
-                    const int r = lane + 32 * k;
+                    const int r = reg_row(lane, k);
                     if (warp < nI && r < m) co[r] = xi[k];
                 }
                 __syncthreads();
