@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--plain-gates", type=int, default=4, help="gates timed on the plain c128 path")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle sample")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--gemm", default="tf32x3", choices=["fp32", "fp32_3m", "tf32x3", "bf16x3"],
+                    help="arithmetic of the merge + gate contraction")
     return ap.parse_args()
 
 
@@ -234,7 +236,8 @@ def run_ours(args, world, rank, local):
     depth = PRESAT + args.warmup + 2 * args.steps + 2
     circ = W.brickwork_su4(N_QUBITS, depth, seed=1000 + rank)
     stream = torch.cuda.Stream(device=dev)
-    m = T.MPS(N_QUBITS, dtype=T.TNSIM_C64, chi_max=CHI, stream=stream.cuda_stream)
+    gemm = getattr(T, "TNSIM_GEMM_" + args.gemm.upper())
+    m = T.MPS(N_QUBITS, dtype=T.TNSIM_C64, chi_max=CHI, gemm=gemm, stream=stream.cuda_stream)
     gdev = [torch.from_numpy(np.ascontiguousarray(l.g4).view(np.float64).copy()).to(dev)
             for l in circ.layers]
     eps_dev = torch.zeros(N_QUBITS, dtype=torch.float64, device=dev)
@@ -381,6 +384,9 @@ def run_ours(args, world, rank, local):
         cfg["parallelism"] = f"replicas x{world}" if world > 1 else "single GPU"
         cfg["jacobi_sweeps_per_gate"] = stats["sweeps"] / max(stats["gates"], 1)
         cfg["interior_chi"] = int(np.max(dims))
+        cfg["contraction"] = {"fp32": "FP32 FMA (4M)", "fp32_3m": "FP32 FMA (3M)",
+                              "tf32x3": "tcgen05 3xTF32, FP32 accumulate",
+                              "bf16x3": "tcgen05 BF16x3, FP32 accumulate"}[args.gemm]
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",

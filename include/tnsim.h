@@ -59,6 +59,15 @@ typedef enum {
     TNSIM_SCHED_PLAIN = 1    /* one pair at a time (the per-pair comparison path) */
 } tnsim_schedule;
 
+/* Arithmetic of the merge + gate contraction for complex64 states (complex128 states
+ * always use FP64 FMA).  The singular value decomposition is FP32 in every mode. */
+typedef enum {
+    TNSIM_GEMM_FP32 = 0,    /* FP32 FMA, four real products per complex product (4M) */
+    TNSIM_GEMM_FP32_3M = 1, /* FP32 FMA, three real products per complex product (3M) */
+    TNSIM_GEMM_TF32X3 = 2,  /* tensor cores (tcgen05 kind::tf32): 3 split TF32 products, FP32 accumulate */
+    TNSIM_GEMM_BF16X3 = 3   /* tensor cores (tcgen05 kind::f16): 3 split BF16 products, FP32 accumulate */
+} tnsim_gemm_mode;
+
 typedef struct {
     int32_t chi_max;    /* bond-dimension cap, >= 1 (Sec. II.A: truncate to a fixed chi) */
     double cutoff;      /* relative discarded-weight cutoff in [0, 1); 0 = none */
@@ -66,9 +75,11 @@ typedef struct {
     int32_t max_sweeps; /* Jacobi sweep cap; 0 = default (40 c64, 60 c128) */
     double jacobi_tol;  /* rotate a column pair while |g| > tol*sqrt(a*b); 0 = default */
     int32_t schedule;   /* tnsim_schedule */
+    int32_t gemm;       /* tnsim_gemm_mode (complex64 only) */
 } tnsim_params;
 
-/* Fill *out with the defaults for dtype dt (chi_max 64, cutoff 0, renormalize 1).
+/* Fill *out with the defaults for dtype dt (chi_max 64, cutoff 0, renormalize 1,
+ * batched schedule, FP32 contraction).
  * Errors: EINVAL if out is NULL or dt unknown. */
 tnsim_status tnsim_params_default(tnsim_dtype dt, tnsim_params* out);
 

@@ -275,6 +275,146 @@ cudaError_t launch_right(const GateDesc* d, int n_gates, int k_max, int n_max, c
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// K1 with three real products per complex product (FP32, SIMT): for a = ar + i ai and
+// b = br + i bi, p1 = ar br, p2 = ai bi, p3 = (ar + ai)(br + bi), so
+// Re(a b) = p1 - p2 and Im(a b) = p3 - p1 - p2; the sums ar + ai and br + bi are formed
+// once per loaded element.  Same tiling and epilogue as k_theta.
+__global__ void __launch_bounds__(256) k_theta_3m(const GateDesc* __restrict__ gd) {
+    using C = float2;
+    const GateDesc& d = gd[blockIdx.z];
+    const int q = d.q;
+    const int chiL = d.chi[q], chiM = d.chi[q + 1], chiR = d.chi[q + 2];
+    const int l0 = blockIdx.x * TH_L, r0 = blockIdx.y * TH_R;
+    if (l0 >= chiL || r0 >= chiR) return;
+    __shared__ __align__(16) float3 As[TH_K][2 * TH_L];   // (re, im, re + im)
+    __shared__ __align__(16) float3 Bs[TH_K][2 * TH_R];
+    __shared__ C Gs[16];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    if (tid < 16) {
+        const int o = tid >> 2, i = tid & 3;
+        double re = 0.0, im = 0.0;
+        for (int j = 0; j < 4; ++j) {
+            double gr = d.g4[2 * (o * 4 + j)], gi = d.g4[2 * (o * 4 + j) + 1];
+            double kr = (j == i) ? 1.0 : 0.0, ki = 0.0;
+            if (d.uL || d.uR) {
+                double ar = ((j >> 1) == (i >> 1)) ? 1.0 : 0.0, ai = 0.0;
+                double br = ((j & 1) == (i & 1)) ? 1.0 : 0.0, bi = 0.0;
+                if (d.uL) { ar = d.uL[2 * ((j >> 1) * 2 + (i >> 1))]; ai = d.uL[2 * ((j >> 1) * 2 + (i >> 1)) + 1]; }
+                if (d.uR) { br = d.uR[2 * ((j & 1) * 2 + (i & 1))]; bi = d.uR[2 * ((j & 1) * 2 + (i & 1)) + 1]; }
+                kr = ar * br - ai * bi; ki = ar * bi + ai * br;
+            }
+            re += gr * kr - gi * ki; im += gr * ki + gi * kr;
+        }
+        Gs[tid].x = (float)re; Gs[tid].y = (float)im;
+    }
+    const C* A = (const C*)d.siteA;
+    const C* B = (const C*)d.siteB;
+    float p1[2][2][2][2], p2[2][2][2][2], p3[2][2][2][2];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        (&p1[0][0][0][0])[i] = 0.f; (&p2[0][0][0][0])[i] = 0.f; (&p3[0][0][0][0])[i] = 0.f;
+    }
+    const int a_row = tid >> 2, a_k = (tid & 3) * 4;
+    const int b_k = tid >> 4, b_seg = tid & 15;
+    const int b_dd = b_seg >> 3, b_r = (b_seg & 7) * 4;
+    const int m = 2 * chiL;
+    for (int k0 = 0; k0 < chiM; k0 += TH_K) {
+        {
+            const int grow = 2 * l0 + a_row;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int k = k0 + a_k + e;
+                C v; v.x = 0; v.y = 0;
+                if (grow < m && k < chiM) v = A[(size_t)grow * chiM + k];
+                As[a_k + e][a_row] = make_float3(v.x, v.y, v.x + v.y);
+            }
+            const int k = k0 + b_k;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int r = r0 + b_r + e;
+                C v; v.x = 0; v.y = 0;
+                if (k < chiM && r < chiR) v = B[((size_t)k * 2 + b_dd) * chiR + r];
+                Bs[b_k][b_dd * TH_R + b_r + e] = make_float3(v.x, v.y, v.x + v.y);
+            }
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < TH_K; ++kk) {
+            float3 a[2][2], b[2][2];
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                a[i][0] = As[kk][2 * (tx + 16 * i)];
+                a[i][1] = As[kk][2 * (tx + 16 * i) + 1];
+            }
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                b[j][0] = Bs[kk][ty + 16 * j];
+                b[j][1] = Bs[kk][TH_R + ty + 16 * j];
+            }
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int j = 0; j < 2; ++j)
+#pragma unroll
+                    for (int c = 0; c < 2; ++c)
+#pragma unroll
+                        for (int e = 0; e < 2; ++e) {
+                            p1[i][j][c][e] = fmaf(a[i][c].x, b[j][e].x, p1[i][j][c][e]);
+                            p2[i][j][c][e] = fmaf(a[i][c].y, b[j][e].y, p2[i][j][c][e]);
+                            p3[i][j][c][e] = fmaf(a[i][c].z, b[j][e].z, p3[i][j][c][e]);
+                        }
+        }
+        __syncthreads();
+    }
+    C* Wm = (C*)d.W;
+    C* T0 = (C*)d.theta0;
+    double fro = 0.0;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const int l = l0 + tx + 16 * i;
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int r = r0 + ty + 16 * j;
+            if (l < chiL && r < chiR) {
+                C acc[2][2];
+#pragma unroll
+                for (int c = 0; c < 2; ++c)
+#pragma unroll
+                    for (int e = 0; e < 2; ++e) {
+                        acc[c][e].x = p1[i][j][c][e] - p2[i][j][c][e];
+                        acc[c][e].y = p3[i][j][c][e] - p1[i][j][c][e] - p2[i][j][c][e];
+                    }
+#pragma unroll
+                for (int bb = 0; bb < 2; ++bb) {
+#pragma unroll
+                    for (int aa = 0; aa < 2; ++aa) {
+                        C t; t.x = 0; t.y = 0;
+#pragma unroll
+                        for (int c = 0; c < 2; ++c)
+#pragma unroll
+                            for (int e = 0; e < 2; ++e) cfma(t, Gs[(2 * aa + bb) * 4 + 2 * c + e], acc[c][e]);
+                        const size_t idx = (size_t)(bb * chiR + r) * m + 2 * l + aa;
+                        Wm[idx] = t;
+                        T0[idx] = t;
+                        fro += (double)t.x * (double)t.x + (double)t.y * (double)t.y;
+                    }
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) fro += __shfl_xor_sync(0xffffffffu, fro, o);
+    if ((tid & 31) == 0 && fro != 0.0) atomicAdd(&d.out->frob2, fro);
+}
+
+cudaError_t launch_theta_3m(const GateDesc* d, int n_gates, int chiL_max, int chiR_max, cudaStream_t s) {
+    if (n_gates <= 0) return cudaSuccess;
+    dim3 grid((chiL_max + TH_L - 1) / TH_L, (chiR_max + TH_R - 1) / TH_R, n_gates);
+    k_theta_3m<<<grid, 256, 0, s>>>(d);
+    return cudaGetLastError();
+}
+
 template cudaError_t launch_theta<float>(const GateDesc*, int, int, int, cudaStream_t);
 template cudaError_t launch_theta<double>(const GateDesc*, int, int, int, cudaStream_t);
 template cudaError_t launch_right<float>(const GateDesc*, int, int, int, cudaStream_t);

@@ -19,6 +19,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>
+
 #include "../../include/tnsim.h"
 #include "tnsim_internal.h"
 
@@ -81,6 +83,11 @@ struct tnsim_mps {
     int* d_sticky = nullptr;
     unsigned long long* d_stats = nullptr;   // 8 counters (tnsim_stats)
     JacobiCtl* d_ctl = nullptr;    // control word of the persistent Jacobi launch
+    // tensor-core contraction (complex64 with gemm TF32X3 / BF16X3)
+    int tc_mode = -1;              // -1 none, 0 TF32 planes, 1 BF16 planes
+    void* d_planes = nullptr;      // [G * 8][tc_rows][tc_k] plane buffer
+    CUtensorMap* d_maps = nullptr; // two tensor maps (A boxes, B boxes)
+    int tc_rows = 0, tc_k = 0;
     GateOut* h_out = nullptr;      // pinned readback
     int* h_chi = nullptr;          // pinned readback
     Staging ring[kRing];
@@ -108,6 +115,7 @@ tnsim_status check_params(const tnsim_params* p) {
     if (!(p->jacobi_tol >= 0.0 && p->jacobi_tol < 1.0)) return fail(TNSIM_EINVAL, "bad jacobi_tol");
     if (p->schedule != TNSIM_SCHED_BATCHED && p->schedule != TNSIM_SCHED_PLAIN)
         return fail(TNSIM_EINVAL, "bad schedule");
+    if (p->gemm < TNSIM_GEMM_FP32 || p->gemm > TNSIM_GEMM_BF16X3) return fail(TNSIM_EINVAL, "bad gemm mode");
     return TNSIM_OK;
 }
 
@@ -117,6 +125,8 @@ void free_all(tnsim_mps* m) {
     cudaFree(m->d_desc); cudaFree(m->d_s1); cudaFree(m->d_gates); cudaFree(m->d_sticky);
     cudaFree(m->d_stats);
     cudaFree(m->d_ctl);
+    cudaFree(m->d_planes);
+    cudaFree(m->d_maps);
     cudaFreeHost(m->h_out); cudaFreeHost(m->h_chi);
     for (auto& r : m->ring) {
         cudaFreeHost(r.desc); cudaFreeHost(r.s1); cudaFreeHost(r.gates);
@@ -234,6 +244,12 @@ tnsim_status upload_desc(cudaStream_t st, const std::vector<GateJob>& jobs, Gate
         d.q = j.q;
         d.chi_max = m->p.chi_max;
         d.renorm = m->p.renormalize ? 1 : 0;
+        d.tc_planes = m->d_planes;
+        d.tc_map_a = m->d_maps;
+        d.tc_map_b = m->d_maps ? m->d_maps + 1 : nullptr;
+        d.tc_slot = j.slot;
+        d.tc_rows = m->tc_rows;
+        d.tc_k = m->tc_k;
     }
     CUDA_TRY(cudaMemcpyAsync(d_desc, h_desc, sizeof(GateDesc) * ng, cudaMemcpyHostToDevice, st));
     return TNSIM_OK;
@@ -244,16 +260,23 @@ tnsim_status launch_gates(cudaStream_t st, const std::vector<GateJob>& jobs, con
                           double tol, int sweeps) {
     const int ng = (int)jobs.size();
     if (ng == 0) return TNSIM_OK;
-    int chiL_max = 1, chiR_max = 1, k_max = 1;
+    int chiL_max = 1, chiM_max = 1, chiR_max = 1, k_max = 1;
     for (const GateJob& j : jobs) {
         chiL_max = std::max(chiL_max, j.m->ub[j.q]);
+        chiM_max = std::max(chiM_max, j.m->ub[j.q + 1]);
         chiR_max = std::max(chiR_max, j.m->ub[j.q + 2]);
         k_max = std::max(k_max, std::min({j.m->cap[j.q + 1], 2 * j.m->ub[j.q], 2 * j.m->ub[j.q + 2]}));
     }
     const int m_max = 2 * chiL_max, n_max = 2 * chiR_max;
     tnsim_mps* pm = jobs[0].m;   // the state whose profiler records this batch
     cudaEvent_t ev = prof_begin(pm, st);
-    CUDA_TRY(launch_theta<T>(d_desc, ng, chiL_max, chiR_max, st));
+    if (sizeof(T) == 8 || pm->p.gemm == TNSIM_GEMM_FP32) {
+        CUDA_TRY(launch_theta<T>(d_desc, ng, chiL_max, chiR_max, st));
+    } else if (pm->p.gemm == TNSIM_GEMM_FP32_3M) {
+        CUDA_TRY(launch_theta_3m(d_desc, ng, chiL_max, chiR_max, st));
+    } else {
+        CUDA_TRY(launch_theta_tc(pm->tc_mode, d_desc, ng, chiL_max, chiM_max, chiR_max, st));
+    }
     prof_end(pm, st, TNSIM_K_THETA, ev);
     CUDA_TRY(cudaMemsetAsync(pm->d_ctl, 0, sizeof(JacobiCtl), st));
     ev = prof_begin(pm, st);
@@ -384,6 +407,7 @@ tnsim_status tnsim_params_default(tnsim_dtype dt, tnsim_params* out) {
     out->max_sweeps = 0;
     out->jacobi_tol = 0.0;
     out->schedule = TNSIM_SCHED_BATCHED;
+    out->gemm = TNSIM_GEMM_FP32;
     return TNSIM_OK;
 }
 
@@ -465,6 +489,23 @@ tnsim_status tnsim_mps_create(int32_t n_qubits, tnsim_dtype dt, const tnsim_para
         if (cudaEventCreateWithFlags(&r.done, cudaEventDisableTiming) != cudaSuccess) {
             free_all(m); delete m;
             return fail(TNSIM_ECUDA, "cudaEventCreate failed");
+        }
+    }
+    if (dt == TNSIM_C64 && (prm.gemm == TNSIM_GEMM_TF32X3 || prm.gemm == TNSIM_GEMM_BF16X3)) {
+        m->tc_mode = prm.gemm == TNSIM_GEMM_TF32X3 ? 0 : 1;
+        m->tc_rows = 2 * m->capmax;
+        m->tc_k = (m->capmax + 63) / 64 * 64;
+        const size_t pbytes = nG * 8 * (size_t)m->tc_rows * m->tc_k * sizeof(float);
+        ALLOC(m->d_planes, pbytes);
+        ALLOC(m->d_maps, 2 * sizeof(CUtensorMap));
+        CUtensorMap hm[2];
+        cudaError_t e1 = cudaMemset(m->d_planes, 0, pbytes);
+        if (e1 == cudaSuccess)
+            e1 = encode_plane_maps(m->tc_mode, m->d_planes, (int)nG, m->tc_rows, m->tc_k, &hm[0], &hm[1]);
+        if (e1 == cudaSuccess) e1 = cudaMemcpy(m->d_maps, hm, sizeof(hm), cudaMemcpyHostToDevice);
+        if (e1 != cudaSuccess) {
+            free_all(m); delete m;
+            return fail(TNSIM_ECUDA, std::string("tensor-core operand set-up: ") + cudaGetErrorString(e1));
         }
     }
 #undef ALLOC
@@ -565,6 +606,7 @@ tnsim_status tnsim_apply_layers_batched(tnsim_mps* const* ms, int32_t n_circ, in
         if (!ms[i]) return fail(TNSIM_EINVAL, "state is NULL");
         if (ms[i]->dt != ms[0]->dt) return fail(TNSIM_EINVAL, "all states must share the dtype");
         if (ms[i]->device != ms[0]->device) return fail(TNSIM_EINVAL, "all states must be on one device");
+        if (ms[i]->p.gemm != ms[0]->p.gemm) return fail(TNSIM_EINVAL, "all states must share the gemm mode");
         for (int j = 0; j < i; ++j)
             if (ms[j] == ms[i]) return fail(TNSIM_EINVAL, "a state appears twice");
     }

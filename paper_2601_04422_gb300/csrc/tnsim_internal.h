@@ -56,11 +56,17 @@ struct GateDesc {
     GateOut* out;
     int* sticky;          // the state's sticky status word (OR of gate statuses)
     unsigned long long* stats;  // the state's 8 work counters (layout of tnsim_stats)
+    // split operand planes for the tensor-core contraction (complex64, TF32X3 / BF16X3)
+    void* tc_planes;      // this state's plane buffer [slots * 8][tc_rows][tc_k]
+    const void* tc_map_a; // CUtensorMap over the planes, 128-row boxes (device memory)
+    const void* tc_map_b; // CUtensorMap over the planes, 64-row boxes (device memory)
     double cutoff;
     int q;
     int chi_max;
     int renorm;
-    int pad_;
+    int tc_slot;          // this gate's slot in the plane buffer
+    int tc_rows;          // rows of every plane (2 * capmax)
+    int tc_k;             // K stride of every plane (capmax rounded up to 64)
 };
 
 // One-qubit update of one site (Eq. 3).
@@ -100,6 +106,15 @@ cudaError_t launch_transfer(const void* site, const int* chi, int q, const doubl
 template <typename T>
 cudaError_t launch_close(const void* E, const void* Rt, const int* chi, int bond, double* out,
                          cudaStream_t s);
+
+// Merge + gate contraction with FP32 3M arithmetic (SIMT).
+cudaError_t launch_theta_3m(const GateDesc* d, int n_gates, int chiL_max, int chiR_max, cudaStream_t s);
+// Tensor-core merge + gate contraction (mode 0: 3xTF32, mode 1: BF16x3), split pass included.
+cudaError_t launch_theta_tc(int mode, const GateDesc* d, int n_gates, int chiL_max, int chiM_max, int chiR_max,
+                            cudaStream_t s);
+// Encode the two tensor maps (opaque 128-byte CUtensorMap values) over a plane buffer.
+cudaError_t encode_plane_maps(int mode, void* planes, int slots, int rows, int kstride, struct CUtensorMap_st* host_a,
+                              struct CUtensorMap_st* host_b);
 
 // Set the thread-local message returned by tnsim_last_error().
 void set_last_error(const char* msg);
