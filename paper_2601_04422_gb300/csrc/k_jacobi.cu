@@ -99,6 +99,46 @@ __device__ __forceinline__ int rotate_pair(C* __restrict__ xi, C* __restrict__ x
     return 1;
 }
 
+// Rotation parameters (c - 1, s e^{i phi}) of a column pair from a, b and g = gr + i gi.
+// The quantities that decide whether the rotation is unitary -- |e^{i phi}| = 1 and
+// c^2 + s^2 = 1 -- use correctly rounded square roots and reciprocals (sqrtf,
+// __frcp_rn), so their rounding errors are unbiased; the skip test and the angle t
+// (which only has to orthogonalise the pair to within rounding) use fast division.
+// c - 1 = -t^2 / (rr (1 + rr)) is formed without cancellation.  FP64 keeps IEEE
+// operations throughout.
+__device__ __forceinline__ bool rot_params_fast(float a, float b, float gr, float gi, float tol2, float zthr,
+                                                float& cm1, float& sr, float& si) {
+    const float g2 = gr * gr + gi * gi;
+    if (!(a > zthr && b > zthr && __fdividef(g2, b) > tol2 * a)) return false;
+    const float rg = __frcp_rn(sqrtf(g2));                // 1 / |g|
+    const float zeta = 0.5f * (b - a) * rg;
+    const float az = fabsf(zeta);
+    // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)); for |zeta| > 2^12, 1 + zeta^2 rounds to zeta^2
+    const float den = az > 4096.f ? 2.f * az : az + sqrtf(fmaf(zeta, zeta, 1.f));
+    const float t = copysignf(__fdividef(1.f, den), zeta);
+    const float rr = sqrtf(fmaf(t, t, 1.f));
+    const float irr = __frcp_rn(rr);                      // c
+    cm1 = -(t * t) * irr * __frcp_rn(1.f + rr);
+    const float sv = t * irr;
+    sr = sv * (gr * rg);
+    si = sv * (gi * rg);
+    return true;
+}
+__device__ __forceinline__ bool rot_params_fast(double a, double b, double gr, double gi, double tol2, double zthr,
+                                                double& cm1, double& sr, double& si) {
+    const double g2 = gr * gr + gi * gi;
+    if (!(a > zthr && b > zthr && g2 / b > tol2 * a)) return false;
+    const double gabs = sqrt(g2);
+    const double zeta = (b - a) / (2 * gabs);
+    const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+    const double rr = sqrt(1.0 + t * t);
+    cm1 = -(t * t) / (rr * (1.0 + rr));
+    const double sv = t / rr;
+    sr = sv * (gr / gabs);
+    si = sv * (gi / gabs);
+    return true;
+}
+
 // Rows owned by a lane in the register-resident layout: element k of a lane is row
 // 64 (k / 2) + 2 lane + (k % 2), so each lane moves two consecutive rows with one
 // 16-byte shared-memory access.
@@ -144,17 +184,9 @@ __device__ __forceinline__ int rotate_reg(C (&xi)[RPL], C* __restrict__ xjs, int
         gr += __shfl_xor_sync(0xffffffffu, gr, o);
         gi += __shfl_xor_sync(0xffffffffu, gi, o);
     }
-    const T g2 = gr * gr + gi * gi;
-    if (!(a > zthr && b > zthr && g2 / b > tol2 * a)) return 0;
-    const T gabs = sqrt(g2);
-    const T zeta = (b - a) / (2 * gabs);
-    const T t = copysign(T(1), zeta) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+    T cm1, sr, si;
+    if (!rot_params_fast(a, b, gr, gi, tol2, zthr, cm1, sr, si)) return 0;
     // same single-rounding update as rotate_pair
-    const T rr = sqrt(T(1) + t * t);
-    const T cm1 = -(t * t) / (rr * (T(1) + rr));
-    const T s = t / rr;
-    const T er = gr / gabs, ei = gi / gabs;
-    const T sr = s * er, si = s * ei;
 #pragma unroll
     for (int k = 0; k < RPL; k += 2) {
         const int r = reg_row(lane, k);
