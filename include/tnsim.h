@@ -130,6 +130,32 @@ tnsim_status tnsim_apply_layers_batched(tnsim_mps* const* ms, int32_t n_circ, in
                                         const double* const* g_ptrs,
                                         const double* const* u1_ptrs);
 
+/* A frozen layer: the descriptors, workspace and launch shapes of one layer of one or
+ * more states, built once so that replaying it needs no host work.  Gate data is read
+ * at replay from the device buffers given here (g4_dev[i]: n2[i]*32 doubles, u1_dev[i]:
+ * n_qubits*8 doubles or NULL), so a caller can refresh their contents between
+ * replays.  Grid shapes are sized for the states' bond capacities, so a plan stays
+ * valid however the bonds grow.  All states must share dtype, device, stream and gemm
+ * mode.  Synchronous (uploads the descriptors).  Errors: EINVAL, ENOMEM, ECUDA. */
+typedef struct tnsim_plan tnsim_plan;
+tnsim_status tnsim_plan_create(tnsim_mps* const* ms, int32_t n_states, const int32_t* n2,
+                               const int32_t* const* q_ptrs, const double* const* g4_dev,
+                               const double* const* u1_dev, tnsim_plan** out);
+
+/* Enqueue a plan's kernels and memsets on the first state's stream (no host
+ * synchronisation, no host copies: it can be captured into a CUDA graph).  The
+ * discarded weights are not returned; tnsim_sync collects the status. */
+tnsim_status tnsim_plan_launch(tnsim_plan* plan);
+tnsim_status tnsim_plan_destroy(tnsim_plan* plan);
+
+/* A CUDA graph holding the launches of n_plans plans in order (captured on the first
+ * plan's stream in relaxed mode), replayed by tnsim_graph_launch on that stream.
+ * Errors: EINVAL, ECUDA. */
+typedef struct tnsim_graph tnsim_graph;
+tnsim_status tnsim_graph_create(tnsim_plan* const* plans, int32_t n_plans, tnsim_graph** out);
+tnsim_status tnsim_graph_launch(tnsim_graph* g);
+tnsim_status tnsim_graph_destroy(tnsim_graph* g);
+
 /* Wait for the handle's stream and return the sticky device status (OK or ENOCONV),
  * clearing it.  Errors: ECUDA. */
 tnsim_status tnsim_sync(tnsim_mps* m);

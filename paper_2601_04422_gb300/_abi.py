@@ -89,6 +89,13 @@ _sig("tnsim_profile_read", C.c_int, [_P, _DP, _I64P])
 _sig("tnsim_two_site_update_noalloc", C.c_int,
      [_P, C.c_int64, _P, C.c_int64, C.c_int32, C.c_int32, C.c_int32, _DP, C.c_int32, C.c_double,
       C.c_int32, _P, _I32P, _DP, _DP])
+_sig("tnsim_plan_create", C.c_int, [C.POINTER(_P), C.c_int32, _I32P, C.POINTER(_I32P), C.POINTER(_P),
+                                     C.POINTER(_P), C.POINTER(_P)])
+_sig("tnsim_plan_launch", C.c_int, [_P])
+_sig("tnsim_plan_destroy", C.c_int, [_P])
+_sig("tnsim_graph_create", C.c_int, [C.POINTER(_P), C.c_int32, C.POINTER(_P)])
+_sig("tnsim_graph_launch", C.c_int, [_P])
+_sig("tnsim_graph_destroy", C.c_int, [_P])
 _sig("tnsim_last_error", C.c_char_p, [])
 _sig("tnsim_version", C.c_char_p, [])
 
@@ -100,7 +107,8 @@ def exported_symbols():
             "tnsim_bond_dims", "tnsim_bond_spectrum", "tnsim_export_sites", "tnsim_import_sites",
             "tnsim_amplitudes", "tnsim_expect_pauli", "tnsim_grad", "tnsim_last_stats",
             "tnsim_profile_enable", "tnsim_profile_read", "tnsim_two_site_update_noalloc",
-            "tnsim_last_error", "tnsim_version"]
+            "tnsim_plan_create", "tnsim_plan_launch", "tnsim_plan_destroy", "tnsim_graph_create",
+            "tnsim_graph_launch", "tnsim_graph_destroy", "tnsim_last_error", "tnsim_version"]
 
 
 def tnsim_last_error() -> str:
@@ -288,6 +296,51 @@ def tnsim_two_site_update_noalloc(site_a: int, cap_a: int, site_b: int, cap_b: i
                                              int(bool(renormalize)), _P(int(stream)) if stream else None,
                                              C.byref(k), C.byref(eps), _dptr(s)))
     return k.value, eps.value, s[: k.value].copy()
+
+
+def tnsim_plan_create(handles, layers):
+    """layers[i] = (q, g4_dev, u1_dev) for state i: host pair list and device pointers
+    (ints; u1_dev may be 0).  Returns the plan handle."""
+    n = len(handles)
+    hs = (_P * n)(*[h.value if isinstance(h, _P) else h for h in handles])
+    n2 = np.zeros(n, dtype=np.int32)
+    qp = (_I32P * n)()
+    gp = (_P * n)()
+    up = (_P * n)()
+    keep = []
+    for i, (q, g, u) in enumerate(layers):
+        q = np.ascontiguousarray(q, dtype=np.int32).reshape(-1)
+        keep.append(q)
+        n2[i] = q.shape[0]
+        qp[i] = q.ctypes.data_as(_I32P)
+        gp[i] = g or None
+        up[i] = u or None
+    out = _P()
+    _check(lib.tnsim_plan_create(hs, n, n2.ctypes.data_as(_I32P), qp, gp, up, C.byref(out)))
+    return out
+
+
+def tnsim_plan_launch(plan):
+    _check(lib.tnsim_plan_launch(plan))
+
+
+def tnsim_plan_destroy(plan):
+    _check(lib.tnsim_plan_destroy(plan))
+
+
+def tnsim_graph_create(plans):
+    arr = (_P * len(plans))(*[p.value for p in plans])
+    out = _P()
+    _check(lib.tnsim_graph_create(arr, len(plans), C.byref(out)))
+    return out
+
+
+def tnsim_graph_launch(graph):
+    _check(lib.tnsim_graph_launch(graph))
+
+
+def tnsim_graph_destroy(graph):
+    _check(lib.tnsim_graph_destroy(graph))
 
 
 class MPS:

@@ -99,6 +99,29 @@ struct tnsim_mps {
     std::vector<Rec> recs;
 };
 
+struct tnsim_plan {
+    std::vector<tnsim_mps*> states;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    tnsim_dtype dt = TNSIM_C64;
+    int gemm = 0, tc_mode = -1;
+    int n_gates = 0, n_s1 = 0;
+    int chiL_max = 1, chiM_max = 1, chiR_max = 1, k_max = 1, caplr = 1;
+    double tol = 0.0;
+    int sweeps = 40;
+    GateDesc* d_desc = nullptr;
+    GateOut* d_out = nullptr;
+    Site1Desc* d_s1 = nullptr;
+    JacobiCtl* d_ctl = nullptr;
+};
+
+struct tnsim_graph {
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
 namespace {
 
 int cap_of(int n, int b, int chi_max) {
@@ -748,6 +771,194 @@ tnsim_status tnsim_apply_layers_batched(tnsim_mps* const* ms, int32_t n_circ, in
     }
     if (worst == 5) return fail(TNSIM_ETIMEOUT, "the Jacobi kernel's idle CTAs saw no progress (step incomplete)");
     if (worst == 4) return fail(TNSIM_ENOCONV, "a Jacobi SVD reached max_sweeps (steps applied)");
+    return TNSIM_OK;
+}
+
+tnsim_status tnsim_plan_create(tnsim_mps* const* ms, int32_t n_states, const int32_t* n2,
+                               const int32_t* const* q_ptrs, const double* const* g4_dev,
+                               const double* const* u1_dev, tnsim_plan** out) {
+    if (!out) return fail(TNSIM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n_states < 1 || !ms || !n2 || !q_ptrs || !g4_dev || !u1_dev) return fail(TNSIM_EINVAL, "bad arguments");
+    for (int i = 0; i < n_states; ++i) {
+        if (!ms[i]) return fail(TNSIM_EINVAL, "state is NULL");
+        if (ms[i]->dt != ms[0]->dt || ms[i]->device != ms[0]->device || ms[i]->stream != ms[0]->stream ||
+            ms[i]->p.gemm != ms[0]->p.gemm)
+            return fail(TNSIM_EINVAL, "the states of a plan must share dtype, device, stream and gemm mode");
+        for (int j = 0; j < i; ++j)
+            if (ms[j] == ms[i]) return fail(TNSIM_EINVAL, "a state appears twice");
+        tnsim_status st = check_pairs(ms[i], n2[i], q_ptrs[i]);
+        if (st != TNSIM_OK) return st;
+        if (n2[i] > 0 && !g4_dev[i]) return fail(TNSIM_EINVAL, "gate pointer is NULL");
+    }
+    tnsim_mps* m0 = ms[0];
+    DevGuard g(m0->device);
+    tnsim_plan* p = new (std::nothrow) tnsim_plan();
+    if (!p) return fail(TNSIM_ENOMEM, "host allocation failed");
+    p->states.assign(ms, ms + n_states);
+    p->stream = m0->stream;
+    p->device = m0->device;
+    p->dt = m0->dt;
+    p->gemm = m0->p.gemm;
+    p->tc_mode = m0->tc_mode;
+    p->tol = m0->p.jacobi_tol;
+    std::vector<GateJob> jobs;
+    std::vector<Site1Desc> s1;
+    for (int i = 0; i < n_states; ++i) {
+        tnsim_mps* m = ms[i];
+        p->sweeps = std::max(p->sweeps, default_sweeps(m));
+        std::vector<char> used(m->n, 0);
+        for (int j = 0; j < n2[i]; ++j) {
+            const int q = q_ptrs[i][j];
+            used[q] = used[q + 1] = 1;
+            GateJob jb;
+            jb.m = m;
+            jb.q = q;
+            jb.slot = j;
+            jb.g4 = g4_dev[i] + (size_t)j * 32;
+            jb.uL = u1_dev[i] ? u1_dev[i] + (size_t)q * 8 : nullptr;
+            jb.uR = u1_dev[i] ? u1_dev[i] + (size_t)(q + 1) * 8 : nullptr;
+            jb.eps_dev = nullptr;
+            jobs.push_back(jb);
+            // launch shapes from the capacities: valid for any bond dimensions reached later
+            p->chiL_max = std::max(p->chiL_max, m->cap[q]);
+            p->chiM_max = std::max(p->chiM_max, m->cap[q + 1]);
+            p->chiR_max = std::max(p->chiR_max, m->cap[q + 2]);
+            p->k_max = std::max(p->k_max, m->cap[q + 1]);
+        }
+        if (u1_dev[i]) {
+            for (int sidx = 0; sidx < m->n; ++sidx) {
+                if (used[sidx]) continue;
+                Site1Desc d;
+                d.site = site_ptr(m, sidx);
+                d.chi = m->d_chi;
+                d.u = u1_dev[i] + (size_t)sidx * 8;
+                d.q = sidx;
+                d.pad_ = 0;
+                s1.push_back(d);
+                p->caplr = std::max(p->caplr, m->cap[sidx] * m->cap[sidx + 1]);
+            }
+        }
+    }
+    std::stable_sort(jobs.begin(), jobs.end(), [](const GateJob& a, const GateJob& b) {
+        const double ca = (double)a.m->cap[a.q] * a.m->cap[a.q + 2] * a.m->cap[a.q + 2];
+        const double cb = (double)b.m->cap[b.q] * b.m->cap[b.q + 2] * b.m->cap[b.q + 2];
+        return ca > cb;
+    });
+    p->n_gates = (int)jobs.size();
+    p->n_s1 = (int)s1.size();
+    cudaError_t e = cudaMalloc((void**)&p->d_desc, sizeof(GateDesc) * (p->n_gates + 1));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&p->d_out, sizeof(GateOut) * (p->n_gates + 1));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&p->d_s1, sizeof(Site1Desc) * (p->n_s1 + 1));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&p->d_ctl, sizeof(JacobiCtl));
+    if (e != cudaSuccess) {
+        cudaFree(p->d_desc); cudaFree(p->d_out); cudaFree(p->d_s1); cudaFree(p->d_ctl);
+        delete p;
+        return fail(TNSIM_ENOMEM, std::string("plan buffers: ") + cudaGetErrorString(e));
+    }
+    std::vector<GateDesc> hd(p->n_gates + 1);
+    if (p->n_gates > 0) {
+        tnsim_status st = upload_desc(p->stream, jobs, hd.data(), p->d_desc, p->d_out);
+        if (st != TNSIM_OK) { tnsim_plan_destroy(p); return st; }
+    }
+    if (p->n_s1 > 0) e = cudaMemcpyAsync(p->d_s1, s1.data(), sizeof(Site1Desc) * p->n_s1, cudaMemcpyHostToDevice, p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) { tnsim_plan_destroy(p); return fail(TNSIM_ECUDA, cudaGetErrorString(e)); }
+    *out = p;
+    return TNSIM_OK;
+}
+
+tnsim_status tnsim_plan_launch(tnsim_plan* p) {
+    if (!p) return fail(TNSIM_EINVAL, "plan is NULL");
+    DevGuard g(p->device);
+    cudaStream_t st = p->stream;
+    if (p->n_s1 > 0) {
+        CUDA_TRY(p->dt == TNSIM_C64 ? launch_site1q<float>(p->d_s1, p->n_s1, p->caplr, st)
+                                    : launch_site1q<double>(p->d_s1, p->n_s1, p->caplr, st));
+    }
+    const int ng = p->n_gates;
+    if (ng == 0) return TNSIM_OK;
+    CUDA_TRY(cudaMemsetAsync(p->d_out, 0, sizeof(GateOut) * ng, st));
+    CUDA_TRY(cudaMemsetAsync(p->d_ctl, 0, sizeof(JacobiCtl), st));
+    const int m_max = 2 * p->chiL_max, n_max = 2 * p->chiR_max;
+    if (p->dt == TNSIM_C128) {
+        CUDA_TRY(launch_theta<double>(p->d_desc, ng, p->chiL_max, p->chiR_max, st));
+        CUDA_TRY(launch_jacobi<double>(p->d_desc, ng, m_max, n_max, p->tol, p->sweeps, p->d_ctl, st));
+        CUDA_TRY(launch_truncate<double>(p->d_desc, ng, st));
+        CUDA_TRY(launch_left<double>(p->d_desc, ng, m_max, p->k_max, st));
+        CUDA_TRY(launch_right<double>(p->d_desc, ng, p->k_max, n_max, st));
+    } else {
+        if (p->gemm == TNSIM_GEMM_FP32) CUDA_TRY(launch_theta<float>(p->d_desc, ng, p->chiL_max, p->chiR_max, st));
+        else if (p->gemm == TNSIM_GEMM_FP32_3M) CUDA_TRY(launch_theta_3m(p->d_desc, ng, p->chiL_max, p->chiR_max, st));
+        else CUDA_TRY(launch_theta_tc(p->tc_mode, p->d_desc, ng, p->chiL_max, p->chiM_max, p->chiR_max, st));
+        CUDA_TRY(launch_jacobi<float>(p->d_desc, ng, m_max, n_max, p->tol, p->sweeps, p->d_ctl, st));
+        CUDA_TRY(launch_truncate<float>(p->d_desc, ng, st));
+        CUDA_TRY(launch_left<float>(p->d_desc, ng, m_max, p->k_max, st));
+        CUDA_TRY(launch_right<float>(p->d_desc, ng, p->k_max, n_max, st));
+    }
+    // the bond upper bounds the host keeps become the capacities
+    for (tnsim_mps* m : p->states)
+        for (int b = 0; b <= m->n; ++b) m->ub[b] = std::max(m->ub[b], m->cap[b]);
+    return TNSIM_OK;
+}
+
+tnsim_status tnsim_plan_destroy(tnsim_plan* p) {
+    if (!p) return TNSIM_OK;
+    DevGuard g(p->device);
+    cudaStreamSynchronize(p->stream);
+    cudaFree(p->d_desc); cudaFree(p->d_out); cudaFree(p->d_s1); cudaFree(p->d_ctl);
+    delete p;
+    return TNSIM_OK;
+}
+
+tnsim_status tnsim_graph_create(tnsim_plan* const* plans, int32_t n_plans, tnsim_graph** out) {
+    if (!out || !plans || n_plans < 1) return fail(TNSIM_EINVAL, "bad arguments");
+    *out = nullptr;
+    for (int i = 0; i < n_plans; ++i)
+        if (!plans[i] || plans[i]->stream != plans[0]->stream) return fail(TNSIM_EINVAL, "plans must share a stream");
+    DevGuard g(plans[0]->device);
+    tnsim_graph* gr = new (std::nothrow) tnsim_graph();
+    if (!gr) return fail(TNSIM_ENOMEM, "host allocation failed");
+    gr->stream = plans[0]->stream;
+    gr->device = plans[0]->device;
+    if (gr->stream == nullptr) { delete gr; return fail(TNSIM_EINVAL, "graphs need a non-default stream"); }
+    CUDA_TRY(cudaStreamSynchronize(gr->stream));
+    cudaError_t e = cudaStreamBeginCapture(gr->stream, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) { delete gr; return fail(TNSIM_ECUDA, std::string("capture: ") + cudaGetErrorString(e)); }
+    tnsim_status st = TNSIM_OK;
+    for (int i = 0; i < n_plans && st == TNSIM_OK; ++i) st = tnsim_plan_launch(plans[i]);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(gr->stream, &graph);
+    if (st != TNSIM_OK || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        delete gr;
+        return st != TNSIM_OK ? st : fail(TNSIM_ECUDA, std::string("capture: ") + cudaGetErrorString(e));
+    }
+    gr->graph = graph;
+    e = cudaGraphInstantiate(&gr->exec, graph, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        delete gr;
+        return fail(TNSIM_ECUDA, std::string("instantiate: ") + cudaGetErrorString(e));
+    }
+    *out = gr;
+    return TNSIM_OK;
+}
+
+tnsim_status tnsim_graph_launch(tnsim_graph* gr) {
+    if (!gr) return fail(TNSIM_EINVAL, "graph is NULL");
+    DevGuard g(gr->device);
+    CUDA_TRY(cudaGraphLaunch(gr->exec, gr->stream));
+    return TNSIM_OK;
+}
+
+tnsim_status tnsim_graph_destroy(tnsim_graph* gr) {
+    if (!gr) return TNSIM_OK;
+    DevGuard g(gr->device);
+    cudaStreamSynchronize(gr->stream);
+    if (gr->exec) cudaGraphExecDestroy(gr->exec);
+    if (gr->graph) cudaGraphDestroy(gr->graph);
+    delete gr;
     return TNSIM_OK;
 }
 

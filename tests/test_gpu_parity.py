@@ -224,6 +224,71 @@ def test_contraction_modes_every_layer(T, mode):
     m.close()
 
 
+@pytest.mark.parametrize("dt,tol", [("C128", 1e-10), ("C64", 1e-5)])
+def test_plans_replayed_as_cuda_graphs(T, dt, tol):
+    """Frozen layers (tnsim_plan) captured into CUDA graphs give the layer-by-layer
+    result: (a) one graph of every layer, replayed once; (b) a graph of two layers
+    (the even and the odd brickwork pattern) replayed four times with the gate buffers
+    refreshed in between."""
+    torch = pytest.importorskip("torch")
+    dtype = getattr(T, "TNSIM_" + dt)
+    circ = W.brickwork_u2_su4(14, 8, seed=12)
+    ref = T.MPS(14, dtype=dtype, chi_max=16)
+    ref.run(circ)
+    want = ref.export_sites()
+    stream = torch.cuda.Stream()
+
+    def dev(a):
+        return torch.from_numpy(np.ascontiguousarray(a).view(np.float64).copy()).cuda()
+
+    # (a) all eight layers in one graph
+    m = T.MPS(14, dtype=dtype, chi_max=16, stream=stream.cuda_stream)
+    bufs = [(dev(l.g4), dev(l.u1)) for l in circ.layers]
+    torch.cuda.synchronize()
+    plans = [T.tnsim_plan_create([m.h], [(l.pairs, g.data_ptr(), u.data_ptr())])
+             for l, (g, u) in zip(circ.layers, bufs)]
+    graph = T.tnsim_graph_create(plans)
+    T.tnsim_graph_launch(graph)
+    m.sync()
+    for a, b in zip(m.export_sites(), want):
+        assert a.shape == b.shape
+    assert 1 - _fidelity(m.export_sites(), want) <= (1e-12 if dt == "C128" else 1e-6)
+    assert _spectrum_err(m, _spec_holder(ref), 16) <= tol
+    T.tnsim_graph_destroy(graph)
+    for p in plans:
+        T.tnsim_plan_destroy(p)
+    m.close()
+
+    # (b) two layers, replayed with refreshed gates
+    m = T.MPS(14, dtype=dtype, chi_max=16, stream=stream.cuda_stream)
+    g_even, u_even = dev(circ.layers[0].g4), dev(circ.layers[0].u1)
+    g_odd, u_odd = dev(circ.layers[1].g4), dev(circ.layers[1].u1)
+    torch.cuda.synchronize()
+    p_even = T.tnsim_plan_create([m.h], [(circ.layers[0].pairs, g_even.data_ptr(), u_even.data_ptr())])
+    p_odd = T.tnsim_plan_create([m.h], [(circ.layers[1].pairs, g_odd.data_ptr(), u_odd.data_ptr())])
+    graph = T.tnsim_graph_create([p_even, p_odd])
+    for t in range(0, 8, 2):
+        with torch.cuda.stream(stream):
+            g_even.copy_(dev(circ.layers[t].g4)); u_even.copy_(dev(circ.layers[t].u1))
+            g_odd.copy_(dev(circ.layers[t + 1].g4)); u_odd.copy_(dev(circ.layers[t + 1].u1))
+        T.tnsim_graph_launch(graph)
+    m.sync()
+    assert 1 - _fidelity(m.export_sites(), want) <= (1e-12 if dt == "C128" else 1e-6)
+    T.tnsim_graph_destroy(graph)
+    T.tnsim_plan_destroy(p_even)
+    T.tnsim_plan_destroy(p_odd)
+    m.close()
+    ref.close()
+
+
+class _spec_holder:
+    """Adapter: exposes a GPU state's bond spectra through the oracle MPS interface."""
+
+    def __init__(self, m):
+        self.n = m.n
+        self.spectrum = [None] + [m.spectrum(b) if len(m.spectrum(b)) else None for b in range(1, m.n)] + [None]
+
+
 # ----------------------------------------------------------------- failures stay on the host
 
 
