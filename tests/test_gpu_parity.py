@@ -486,6 +486,51 @@ def test_c2_complex64_every_layer(T):
     m.close()
 
 
+# ----------------------------------------------------------------- the gate-set workload (C3)
+
+
+@pytest.mark.parametrize("mode", ["FP32_3M", "TF32X3", "BF16X3"])
+def test_c3_gate_set_exact_width(T, mode):
+    """{H, CX, RZZ(t), RX(t)} drawn per site, depth 24, chi_max 256, at 16 qubits where no
+    bond can exceed 256: every contraction mode against the dense state vector."""
+    circ = W.gateset_circuit(16, 24, seed=1)
+    m = T.MPS(16, dtype=T.TNSIM_C64, chi_max=256, gemm=getattr(T, "TNSIM_GEMM_" + mode))
+    m.run(circ)
+    psi = dense.run_circuit(circ)
+    got = om.to_dense(om.MPS(m.export_sites()))
+    F = abs(np.vdot(got, psi)) ** 2 / (np.vdot(got, got).real * np.vdot(psi, psi).real)
+    assert 1 - F <= 1e-6
+    bits = W.random_bitstrings(16, 256, seed=4)
+    idx = bits.astype(np.int64) @ (1 << np.arange(15, -1, -1))
+    a = m.amplitudes(bits)
+    assert np.linalg.norm(a - psi[idx]) / np.linalg.norm(psi[idx]) <= 2e-3
+    m.close()
+
+
+@pytest.mark.slow
+def test_c3_full_size_last_layer(T):
+    """100 qubits, depth 24, the gate set, chi_max 256, 3xTF32 contraction: the last layer
+    (one-qubit draws fused or applied on their own, CX and RZZ pairs) against the oracle
+    applied to the same exported input state -- every gate's kept singular values and the
+    fidelity of the whole state after the layer."""
+    circ, p = W.config_c3(1)
+    m = T.MPS(100, dtype=T.TNSIM_C64, chi_max=p["chi_max"], gemm=T.TNSIM_GEMM_TF32X3)
+    for lay in circ.layers[:-1]:
+        m.apply_layer(lay)
+    pre = om.MPS(m.export_sites())
+    last = circ.layers[-1]
+    m.apply_layer(last)
+    recs = om.apply_layer(pre, last, p["chi_max"])
+    for r in recs:
+        sg = m.spectrum(r.q + 1)
+        k = max(len(sg), r.k)
+        a = np.zeros(k); a[: len(sg)] = sg
+        b = np.zeros(k); b[: r.k] = r.s_kept
+        assert np.max(np.abs(a - b)) / r.s_kept[0] <= 1e-5
+    assert 1 - om.fidelity(om.MPS(m.export_sites()), pre) <= 1e-6
+    m.close()
+
+
 # ----------------------------------------------------------------- full size, sampled gates
 
 
