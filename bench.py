@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--plain-gates", type=int, default=4, help="gates timed on the plain c128 path")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle sample")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--nonlocal-ops", type=int, default=60,
+                    help="gates at distance <= 6 applied to the saturated state by the SWAP method")
     ap.add_argument("--gemm", default="tf32x3", choices=["fp32", "fp32_3m", "tf32x3", "bf16x3"],
                     help="arithmetic of the merge + gate contraction")
     return ap.parse_args()
@@ -371,6 +373,24 @@ def run_ours(args, world, rank, local):
                  "jacobi_sweeps_per_gate": st_p["sweeps"] / max(st_p["gates"], 1)}
         mp.close()
 
+    # ---- non-local gates (SWAP method, tnsim_apply_circuit) on the same saturated state
+    nonlocal_obj = None
+    if args.nonlocal_ops > 0 and rank == 0:
+        mn = T.MPS(N_QUBITS, dtype=T.TNSIM_C64, chi_max=CHI, gemm=gemm, stream=stream.cuda_stream)
+        mn.import_sites(m.export_sites())
+        ops = W.nonlocal_ops(N_QUBITS, args.nonlocal_ops, seed=7, p1=0.0, max_dist=6)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        n_layers, n_local, _ = mn.apply_circuit(ops)
+        tn = time.perf_counter() - t0
+        nonlocal_obj = {"value": n_local / tn, "unit": "local 2q updates/s (SWAPs included)",
+                        "ops_per_s": len(ops) / tn, "ops": len(ops), "local_updates": n_local,
+                        "layers": n_layers, "seconds": tn,
+                        "sample": f"{len(ops)} Haar U(4) gates at distance 1-6 in either qubit order on the "
+                                  f"saturated chi {CHI} state, one synchronous tnsim_apply_circuit call "
+                                  "(gate upload and read-back included)"}
+        mn.close()
+
     cpu = None
     if rank == 0 and world == 1 and args.cpu_seconds > 0:
         r, gcount, secs = oracle_gate_rate(args.cpu_seconds)
@@ -392,7 +412,8 @@ def run_ours(args, world, rank, local):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": cfg, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e_obj,
                 "gpu_launches": launches, "clocks": clocks, "plain_path": plain,
-                "vs_plain": (value / plain["value"]) if plain else None, "kernels": kernels}
+                "vs_plain": (value / plain["value"]) if plain else None, "kernels": kernels,
+                "nonlocal": nonlocal_obj}
         print(json.dumps(line), flush=True)
     m.close()
     if dist:

@@ -118,6 +118,45 @@ tnsim_status tnsim_apply_layer_device(tnsim_mps* m, int32_t n2, const int32_t* q
                                       const double* g4x4_dev, const double* u1_dev,
                                       double* eps_dev);
 
+/* Apply a list of gates on any qubits (Sec. III.B: non-local two-qubit gates by the
+ * SWAP method, and layerization into non-overlapping layers).
+ *   operation i : qb[i] < 0 -- a one-qubit gate on qubit qa[i], 2x2 in the first 8
+ *                 doubles of mats[32*i ...];
+ *                 qb[i] >= 0 -- a two-qubit gate on the distinct qubits qa[i], qb[i]
+ *                 (any distance, either order), 4x4 in mats[32*i ...] with basis
+ *                 index 2*b_qa + b_qb.
+ * A gate on qubits lo < hi with hi - lo > 1 runs as: SWAP(hi-1, hi), ...,
+ * SWAP(lo+1, lo+2), the gate on (lo, lo+1), then the same SWAPs in reverse order;
+ * each SWAP is an ordinary truncating two-qubit update.  The local operations are
+ * cut into layers as soon as possible (one-qubit gates share a layer with the
+ * next two-qubit gate on their qubit), which gives the same state as applying the
+ * list in order.  n_layers_out / n_gates_out (may be NULL) receive the number of
+ * layers and of local two-qubit updates (SWAPs included); eps_sum_out (may be
+ * NULL) the sum of their discarded weights.  The gate data is copied to the device
+ * once (a stream-ordered allocation freed at the end); the layers are launched back
+ * to back without host synchronisation; the call synchronises at the end.
+ * Errors: EINVAL (bad qubit, equal qubits, non-finite entry; nothing launched),
+ * ENOCONV (applied; an SVD hit max_sweeps), ETIMEOUT (state undefined), ECUDA. */
+tnsim_status tnsim_apply_circuit(tnsim_mps* m, int32_t n_ops, const int32_t* qa, const int32_t* qb,
+                                 const double* mats, int32_t* n_layers_out, int32_t* n_gates_out,
+                                 double* eps_sum_out);
+
+/* The host planner of tnsim_apply_circuit on its own (no GPU work, no handle):
+ * expand the same operation list (n_qubits qubits) into layers.  n_layers and
+ * n_gates (required) receive the sizes.  If layer_n2, gate_q, gate_g4 and layer_u1
+ * are all NULL only the sizes are computed; otherwise every one must be given with
+ * cap_layers >= *n_layers and cap_gates >= *n_gates:
+ *   layer_n2 [n_layers]        pairs per layer;
+ *   gate_q   [n_gates]         left qubit of each pair, layer after layer;
+ *   gate_g4  [n_gates * 32]    the 4x4 of each pair (basis 2*b_q + b_{q+1});
+ *   layer_u1 [n_layers * n_qubits * 8]  the one-qubit gates of each layer, applied
+ *                              before its pairs (identity where none).
+ * Errors: EINVAL (bad operation, capacity too small). */
+tnsim_status tnsim_circuit_layerize(int32_t n_qubits, int32_t n_ops, const int32_t* qa, const int32_t* qb,
+                                    const double* mats, int32_t cap_layers, int32_t cap_gates,
+                                    int32_t* n_layers, int32_t* n_gates, int32_t* layer_n2,
+                                    int32_t* gate_q, double* gate_g4, double* layer_u1);
+
 /* Apply layers to several independent states in one batched schedule: for each
  * step t in [0, n_steps), state ms[i] gets the layer described by
  * (n2[t*n_circ+i], q_ptrs[...], g_ptrs[...], u1_ptrs[...]) -- all host arrays in

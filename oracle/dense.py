@@ -43,6 +43,29 @@ def apply_2q(psi: np.ndarray, n: int, q: int, g: np.ndarray) -> np.ndarray:
     return t.reshape(-1)
 
 
+def apply_2q_any(psi: np.ndarray, n: int, qa: int, qb: int, g: np.ndarray) -> np.ndarray:
+    """Contract a rank-4 gate tensor with legs (qa, qb) of the state, any two distinct
+    qubits in either order (Eq. 1, U^(2) on non-adjacent legs); ``g`` has basis index
+    2*b_qa + b_qb."""
+    t = psi.reshape((2,) * n)
+    G = g.reshape(2, 2, 2, 2)
+    t = np.tensordot(G, t, axes=([2, 3], [qa, qb]))
+    t = np.moveaxis(t, [0, 1], [qa, qb])
+    return t.reshape(-1)
+
+
+def run_ops(n: int, ops) -> np.ndarray:
+    """A gate list in program order; (qa, qb, matrix) with qb None or < 0 for one qubit."""
+    psi = zero_state(n)
+    for qa, qb, g in ops:
+        g = np.asarray(g, dtype=np.complex128)
+        if qb is None or qb < 0:
+            psi = apply_1q(psi, n, int(qa), g)
+        else:
+            psi = apply_2q_any(psi, n, int(qa), int(qb), g)
+    return psi
+
+
 def run_circuit(circuit) -> np.ndarray:
     """Apply every layer: the layer's one-qubit gates first, then its two-qubit gates."""
     n = circuit.n_qubits

@@ -161,6 +161,58 @@ def apply_layer(mps: MPS, layer, chi_max: int, cutoff: float = 0.0,
     return recs
 
 
+# SWAP on an adjacent pair in the basis 2 b_q + b_{q+1}
+SWAP = np.array([[1, 0, 0, 0],
+                 [0, 0, 1, 0],
+                 [0, 1, 0, 0],
+                 [0, 0, 0, 1]], dtype=np.complex128)
+
+
+def reversed_pair(g: np.ndarray) -> np.ndarray:
+    """The 4x4 of the same gate with its two qubits named in the other order:
+    as a tensor G[a, b, c, d] (outputs a, b; inputs c, d) both pairs of legs swap."""
+    return g.reshape(2, 2, 2, 2).transpose(1, 0, 3, 2).reshape(4, 4)
+
+
+def apply_2q_any(mps: MPS, qa: int, qb: int, g: np.ndarray, chi_max: int, cutoff: float = 0.0,
+                 renormalize: bool = True) -> List[GateRecord]:
+    """Two-qubit gate on any two distinct qubits by the SWAP method (Sec. III.B
+    simulation_kernel: SWAP gates make the distant sites local, the gate is applied,
+    and the SWAPs are reversed).  ``g`` has basis index 2*b_qa + b_qb.
+
+    Reading of "move the distant sites": the qubit farther right, hi, moves left by
+    SWAPs on (hi-1, hi), (hi-2, hi-1), ..., (lo+1, lo+2) until it sits at lo+1; the
+    gate acts on (lo, lo+1); the same SWAPs then run in reverse order.  Every SWAP is
+    an ordinary truncating two-qubit update.  Returns one record per update."""
+    if qa == qb:
+        raise ValueError("the two qubits must differ")
+    lo, hi, gl = (qa, qb, g) if qa < qb else (qb, qa, reversed_pair(g))
+    recs = []
+    for j in range(hi - 1, lo, -1):
+        recs.append(apply_2q(mps, j, SWAP, chi_max, cutoff, renormalize))
+    recs.append(apply_2q(mps, lo, gl, chi_max, cutoff, renormalize))
+    for j in range(lo + 1, hi):
+        recs.append(apply_2q(mps, j, SWAP, chi_max, cutoff, renormalize))
+    return recs
+
+
+def run_ops(n: int, ops, chi_max: int, cutoff: float = 0.0, renormalize: bool = True,
+            mps: Optional[MPS] = None):
+    """Apply a gate list in program order from |0...0> (or from ``mps``).  ``ops`` holds
+    (qa, qb, matrix) with qb None or negative for a one-qubit gate.  Returns
+    (mps, records of every two-qubit update, SWAPs included)."""
+    if mps is None:
+        mps = zero_state(n)
+    recs = []
+    for qa, qb, g in ops:
+        g = np.asarray(g, dtype=np.complex128)
+        if qb is None or qb < 0:
+            apply_1q(mps, int(qa), g)
+        else:
+            recs += apply_2q_any(mps, int(qa), int(qb), g, chi_max, cutoff, renormalize)
+    return mps, recs
+
+
 def run_circuit(circuit, chi_max: int, cutoff: float = 0.0, renormalize: bool = True,
                 mps: Optional[MPS] = None):
     """Run every layer from |0...0> (or from ``mps``); returns (mps, records per layer)."""

@@ -15,6 +15,7 @@ from ._abi import (  # noqa: F401
     tnsim_expect_pauli, tnsim_grad, tnsim_last_stats, tnsim_last_error, tnsim_version,
     tnsim_stats, tnsim_profile_enable, tnsim_profile_read, TNSIM_K_NAMES,
     tnsim_two_site_update_noalloc, tnsim_plan_create, tnsim_plan_launch, tnsim_plan_destroy,
-    tnsim_graph_create, tnsim_graph_launch, tnsim_graph_destroy,
+    tnsim_graph_create, tnsim_graph_launch, tnsim_graph_destroy, tnsim_apply_circuit,
+    tnsim_circuit_layerize,
     MPS,
 )

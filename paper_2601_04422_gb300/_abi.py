@@ -96,6 +96,9 @@ _sig("tnsim_plan_destroy", C.c_int, [_P])
 _sig("tnsim_graph_create", C.c_int, [C.POINTER(_P), C.c_int32, C.POINTER(_P)])
 _sig("tnsim_graph_launch", C.c_int, [_P])
 _sig("tnsim_graph_destroy", C.c_int, [_P])
+_sig("tnsim_apply_circuit", C.c_int, [_P, C.c_int32, _I32P, _I32P, _DP, _I32P, _I32P, _DP])
+_sig("tnsim_circuit_layerize", C.c_int, [C.c_int32, C.c_int32, _I32P, _I32P, _DP, C.c_int32, C.c_int32,
+                                         _I32P, _I32P, _I32P, _I32P, _DP, _DP])
 _sig("tnsim_last_error", C.c_char_p, [])
 _sig("tnsim_version", C.c_char_p, [])
 
@@ -108,7 +111,8 @@ def exported_symbols():
             "tnsim_amplitudes", "tnsim_expect_pauli", "tnsim_grad", "tnsim_last_stats",
             "tnsim_profile_enable", "tnsim_profile_read", "tnsim_two_site_update_noalloc",
             "tnsim_plan_create", "tnsim_plan_launch", "tnsim_plan_destroy", "tnsim_graph_create",
-            "tnsim_graph_launch", "tnsim_graph_destroy", "tnsim_last_error", "tnsim_version"]
+            "tnsim_graph_launch", "tnsim_graph_destroy", "tnsim_apply_circuit", "tnsim_circuit_layerize",
+            "tnsim_last_error", "tnsim_version"]
 
 
 def tnsim_last_error() -> str:
@@ -173,6 +177,55 @@ def tnsim_apply_layer_device(h, q, g4x4_dev: int, u1_dev: int = 0, eps_dev: int 
     q = np.ascontiguousarray(q, dtype=np.int32).reshape(-1)
     _check(lib.tnsim_apply_layer_device(h, q.shape[0], q.ctypes.data_as(_I32P), _P(g4x4_dev or None),
                                         _P(u1_dev or None), _P(eps_dev or None)))
+
+
+def _ops_arrays(ops):
+    """ops: sequence of (qa, qb, matrix) with qb None or < 0 for a one-qubit gate (2x2)."""
+    n = len(ops)
+    qa = np.zeros(max(n, 1), np.int32)
+    qb = np.zeros(max(n, 1), np.int32)
+    mats = np.zeros((max(n, 1), 16), np.complex128)
+    for i, (a, b, g) in enumerate(ops):
+        g = np.asarray(g, dtype=np.complex128)
+        qa[i] = int(a)
+        if b is None or int(b) < 0:
+            qb[i] = -1
+            mats[i, :4] = g.reshape(4)
+        else:
+            qb[i] = int(b)
+            mats[i] = g.reshape(16)
+    return n, qa, qb, mats.view(np.float64)
+
+
+def tnsim_apply_circuit(h, ops):
+    """Apply a gate list on any qubits; returns (n_layers, n_local_gates, eps_sum)."""
+    n, qa, qb, md = _ops_arrays(ops)
+    nl, ng, eps = C.c_int32(0), C.c_int32(0), C.c_double(0.0)
+    _check(lib.tnsim_apply_circuit(h, n, qa.ctypes.data_as(_I32P), qb.ctypes.data_as(_I32P), _dptr(md),
+                                   C.byref(nl), C.byref(ng), C.byref(eps)))
+    return nl.value, ng.value, eps.value
+
+
+def tnsim_circuit_layerize(n_qubits: int, ops):
+    """The host planner alone: returns a list of layers (pairs, g4 [n2,4,4], u1 [n,2,2])."""
+    n, qa, qb, md = _ops_arrays(ops)
+    nl, ng = C.c_int32(0), C.c_int32(0)
+    args = (int(n_qubits), n, qa.ctypes.data_as(_I32P), qb.ctypes.data_as(_I32P), _dptr(md))
+    _check(lib.tnsim_circuit_layerize(*args, 0, 0, C.byref(nl), C.byref(ng), None, None, None, None))
+    L, G = nl.value, ng.value
+    n2 = np.zeros(max(L, 1), np.int32)
+    gq = np.zeros(max(G, 1), np.int32)
+    g4 = np.zeros((max(G, 1), 4, 4), np.complex128)
+    u1 = np.zeros((max(L, 1), int(n_qubits), 2, 2), np.complex128)
+    _check(lib.tnsim_circuit_layerize(*args, L, G, C.byref(nl), C.byref(ng), n2.ctypes.data_as(_I32P),
+                                      gq.ctypes.data_as(_I32P), _dptr(g4.view(np.float64)),
+                                      _dptr(u1.view(np.float64))))
+    out, off = [], 0
+    for i in range(L):
+        k = int(n2[i])
+        out.append((gq[off:off + k].copy(), g4[off:off + k].copy(), u1[i].copy()))
+        off += k
+    return out
 
 
 def tnsim_apply_layers_batched(handles, steps):
@@ -374,6 +427,9 @@ class MPS:
 
     def run(self, circuit):
         return [self.apply_layer(l) for l in circuit.layers]
+
+    def apply_circuit(self, ops):
+        return tnsim_apply_circuit(self.h, ops)
 
     def bond_dims(self):
         return tnsim_bond_dims(self.h, self.n)

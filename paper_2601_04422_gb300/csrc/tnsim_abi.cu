@@ -22,6 +22,7 @@
 #include <cuda.h>
 
 #include "../../include/tnsim.h"
+#include "tnsim_circuit.h"
 #include "tnsim_internal.h"
 
 using namespace tnsim;
@@ -616,6 +617,69 @@ tnsim_status tnsim_apply_layer(tnsim_mps* m, int32_t n2, const int32_t* q, const
     if (worst) CUDA_TRY(cudaMemset(m->d_sticky, 0, sizeof(int)));
     if (worst == 5) return fail(TNSIM_ETIMEOUT, "the Jacobi kernel's idle CTAs saw no progress (layer incomplete)");
     if (worst == 4) return fail(TNSIM_ENOCONV, "a Jacobi SVD reached max_sweeps (layer applied)");
+    return TNSIM_OK;
+}
+
+tnsim_status tnsim_apply_circuit(tnsim_mps* m, int32_t n_ops, const int32_t* qa, const int32_t* qb,
+                                 const double* mats, int32_t* n_layers_out, int32_t* n_gates_out,
+                                 double* eps_sum_out) {
+    if (!m) return fail(TNSIM_EINVAL, "state is NULL");
+    DevGuard g(m->device);
+    tnsim::CircuitLayers cl;
+    std::string err;
+    tnsim_status s = tnsim::layerize_circuit(m->n, n_ops, qa, qb, mats, cl, err);
+    if (s != TNSIM_OK) return fail(s, err);
+    const int nl = (int)cl.n2.size(), ng = (int)cl.q.size();
+    if (n_layers_out) *n_layers_out = nl;
+    if (n_gates_out) *n_gates_out = ng;
+    if (eps_sum_out) *eps_sum_out = 0.0;
+    if (nl == 0) return TNSIM_OK;
+    for (int L = 0; L < nl; ++L) {
+        s = check_pairs(m, cl.n2[L], cl.q.data() + cl.q_off[L]);
+        if (s != TNSIM_OK) return s;
+    }
+    // every gate of the list on the device at once: the 4x4s, the one-qubit layers in
+    // use and one discarded weight per local two-qubit gate
+    int nu = 0;
+    for (char h : cl.has_u1) nu += h ? 1 : 0;
+    const size_t n8 = (size_t)m->n * 8;
+    std::vector<double> hbuf((size_t)ng * 32 + (size_t)nu * n8);
+    std::memcpy(hbuf.data(), cl.g4.data(), sizeof(double) * cl.g4.size());
+    for (int L = 0, ui = 0; L < nl; ++L)
+        if (cl.has_u1[L]) std::memcpy(hbuf.data() + (size_t)ng * 32 + (size_t)(ui++) * n8, cl.u1.data() + L * n8,
+                                      sizeof(double) * n8);
+    double* dbuf = nullptr;
+    CUDA_TRY(cudaMallocAsync((void**)&dbuf, sizeof(double) * (hbuf.size() + ng), m->stream));
+    double* d_g4 = dbuf;
+    double* d_u1 = dbuf + (size_t)ng * 32;
+    double* d_eps = d_u1 + (size_t)nu * n8;
+    // from pageable memory: returns once hbuf has been consumed
+    CUDA_TRY(cudaMemcpyAsync(dbuf, hbuf.data(), sizeof(double) * hbuf.size(), cudaMemcpyHostToDevice, m->stream));
+    CUDA_TRY(cudaMemsetAsync(d_eps, 0, sizeof(double) * ng, m->stream));
+    for (int L = 0, ui = 0; L < nl; ++L) {
+        Staging* stg = acquire_staging(m);
+        const double* u1 = cl.has_u1[L] ? d_u1 + (size_t)(ui++) * n8 : nullptr;
+        s = enqueue_layer(m, stg, cl.n2[L], cl.q.data() + cl.q_off[L], d_g4 + (size_t)cl.q_off[L] * 32, u1,
+                          d_eps + cl.q_off[L]);
+        CUDA_TRY(cudaEventRecord(stg->done, m->stream));
+        if (s != TNSIM_OK) {
+            cudaFreeAsync(dbuf, m->stream);
+            return s;
+        }
+    }
+    std::vector<double> eps((size_t)ng);
+    int sticky = 0;
+    CUDA_TRY(cudaMemcpyAsync(eps.data(), d_eps, sizeof(double) * ng, cudaMemcpyDeviceToHost, m->stream));
+    CUDA_TRY(cudaMemcpyAsync(&sticky, m->d_sticky, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
+    CUDA_TRY(cudaFreeAsync(dbuf, m->stream));
+    s = refresh_dims(m);   // synchronises
+    if (s != TNSIM_OK) return s;
+    double tot = 0.0;
+    for (double e : eps) tot += e;
+    if (eps_sum_out) *eps_sum_out = tot;
+    if (sticky) CUDA_TRY(cudaMemset(m->d_sticky, 0, sizeof(int)));
+    if (sticky == 5) return fail(TNSIM_ETIMEOUT, "the Jacobi kernel's idle CTAs saw no progress (circuit incomplete)");
+    if (sticky == 4) return fail(TNSIM_ENOCONV, "a Jacobi SVD reached max_sweeps (circuit applied)");
     return TNSIM_OK;
 }
 

@@ -32,7 +32,7 @@ __all__ = [
     "gate_rzz", "gate_cp", "PAULI",
     "brickwork_su4", "brickwork_u2_su4", "gateset_circuit", "hea_circuit",
     "ghz_circuit", "qft_nn_circuit", "batch_circuits", "random_sites",
-    "random_bitstrings", "config_c1", "config_c2", "config_c3",
+    "random_bitstrings", "config_c1", "config_c2", "config_c3", "nonlocal_ops",
 ]
 
 
@@ -326,6 +326,26 @@ def batch_circuits(n_circ: int, base_seed: int = 1000):
         c.meta["chi_max"] = chi
         out.append((c, chi))
     return out
+
+
+def nonlocal_ops(n: int, n_ops: int, seed: int, p1: float = 0.25, max_dist: Optional[int] = None):
+    """A gate list on arbitrary qubits: with probability p1 a Haar U(2) on a uniform
+    qubit, else a Haar U(4) on two distinct qubits at distance <= max_dist (default
+    n - 1), in random order (either may be the first listed).  Items are
+    (qa, qb, matrix) with qb None for one-qubit gates; a two-qubit matrix has basis
+    index 2*b_qa + b_qb."""
+    rng = np.random.default_rng(seed)
+    dmax = n - 1 if max_dist is None else max(1, min(int(max_dist), n - 1))
+    ops = []
+    for _ in range(n_ops):
+        if rng.random() < p1:
+            ops.append((int(rng.integers(n)), None, haar_unitary(2, rng)))
+            continue
+        d = int(rng.integers(1, dmax + 1))
+        lo = int(rng.integers(0, n - d))
+        a, b = (lo, lo + d) if rng.random() < 0.5 else (lo + d, lo)
+        ops.append((a, b, haar_unitary(4, rng)))
+    return ops
 
 
 def random_sites(chi_l: int, chi_m: int, chi_r: int, seed: int):
