@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--plain-gates", type=int, default=4, help="gates timed on the plain c128 path")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle sample")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--shots", type=int, default=1024, help="perfect-sampling shots on the saturated state")
     ap.add_argument("--nonlocal-ops", type=int, default=60,
                     help="gates at distance <= 6 applied to the saturated state by the SWAP method")
     ap.add_argument("--gemm", default="tf32x3", choices=["fp32", "fp32_3m", "tf32x3", "bf16x3"],
@@ -391,6 +392,21 @@ def run_ours(args, world, rank, local):
                                   "(gate upload and read-back included)"}
         mn.close()
 
+    # ---- perfect sampling (tnsim_sample) of the same saturated state
+    sampling_obj = None
+    if args.shots > 0 and rank == 0:
+        u = np.random.default_rng(17).random((args.shots, N_QUBITS))
+        T.tnsim_sample(m.h, u[:8])          # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, nodes = T.tnsim_sample(m.h, u)
+        ts = time.perf_counter() - t0
+        sampling_obj = {"value": args.shots / ts, "unit": "shots/s", "shots": args.shots, "seconds": ts,
+                        "prefixes_evaluated": nodes, "prefixes_without_memoisation": args.shots * N_QUBITS,
+                        "sample": f"{args.shots} bitstrings of the saturated {N_QUBITS}-qubit chi {CHI} state, "
+                                  "one synchronous tnsim_sample call (right environments, uniforms upload "
+                                  "and bit read-back included)"}
+
     cpu = None
     if rank == 0 and world == 1 and args.cpu_seconds > 0:
         r, gcount, secs = oracle_gate_rate(args.cpu_seconds)
@@ -413,7 +429,7 @@ def run_ours(args, world, rank, local):
                 "config": cfg, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e_obj,
                 "gpu_launches": launches, "clocks": clocks, "plain_path": plain,
                 "vs_plain": (value / plain["value"]) if plain else None, "kernels": kernels,
-                "nonlocal": nonlocal_obj}
+                "nonlocal": nonlocal_obj, "sampling": sampling_obj}
         print(json.dumps(line), flush=True)
     m.close()
     if dist:

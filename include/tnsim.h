@@ -230,6 +230,23 @@ tnsim_status tnsim_amplitudes(tnsim_mps* m, int64_t n_str, const uint8_t* bits,
 tnsim_status tnsim_expect_pauli(tnsim_mps* m, int32_t n_terms, const char* paulis,
                                 double* out);
 
+/* Perfect sampling of n_shots bitstrings (Sec. III.A "Sampling"; Sec. III.B
+ * measurement).  Qubit by qubit from qubit 0, shot s takes bit b_q = 1 exactly when
+ * uniforms[s*n + q] * (p0 + p1) >= p0, where p0, p1 are the weights of the two
+ * outcomes given its earlier bits; the prefix is then projected on the outcome
+ * and renormalised.  The weights use the right environments of the state, which
+ * gives the same numbers as sampling its right-canonical form.  Shots with the
+ * same prefix share its vector (memoised prefixes): each site evaluates only the
+ * distinct prefixes.
+ *   uniforms : host, n_shots * n_qubits doubles in [0, 1), row s = shot s;
+ *   bits_out : host, n_shots * n_qubits bytes (0/1), qubit 0 first;
+ *   n_nodes_out (may be NULL): distinct prefixes evaluated, summed over the sites.
+ * Work buffers come from one stream-ordered allocation freed at the end.
+ * Synchronous.  Errors: EINVAL (n_shots outside [0, 2^24], NULL, a uniform outside
+ * [0, 1)), ECUDA. */
+tnsim_status tnsim_sample(tnsim_mps* m, int64_t n_shots, const double* uniforms, uint8_t* bits_out,
+                          int64_t* n_nodes_out);
+
 /* Gradient of an energy with respect to gate angles: not in this build
  * (returns EUNSUPPORTED). All pointer arguments are ignored. */
 tnsim_status tnsim_grad(const void* circuit, const double* theta, int32_t n_theta,

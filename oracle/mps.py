@@ -307,22 +307,31 @@ def right_canonicalize(mps: MPS) -> MPS:
     return out
 
 
-def perfect_sample(mps: MPS, n_shots: int, rng: np.random.Generator) -> np.ndarray:
-    """Perfect sampling (Sec. III.A "Sampling"): draw each qubit from its marginal
-    conditioned on the bits already drawn, project, renormalise.  Plain version
-    without memoisation.  Returns uint8 [n_shots, n]."""
+def perfect_sample_u(mps: MPS, u: np.ndarray) -> np.ndarray:
+    """Perfect sampling (Sec. III.A "Sampling"; Sec. III.B: canonicalise, then sample)
+    with the random draws given: shot s takes bit b_q = 1 exactly when
+    u[s, q] * (p0 + p1) >= p0, where p0, p1 are the weights of the two outcomes of
+    qubit q given the bits already drawn.  After each draw the prefix is projected on
+    its outcome and renormalised.  Plain version: no memoisation.  Returns uint8
+    [n_shots, n]."""
+    u = np.asarray(u, dtype=np.float64)
     rc = right_canonicalize(mps)
     nrm = np.sqrt(norm2(rc))
-    out = np.zeros((n_shots, rc.n), dtype=np.uint8)
-    for s in range(n_shots):
+    out = np.zeros((u.shape[0], rc.n), dtype=np.uint8)
+    for s in range(u.shape[0]):
         v = np.ones((1,), dtype=np.complex128) / nrm
         for q, a in enumerate(rc.sites):
             w0 = v @ a[:, 0, :]
             w1 = v @ a[:, 1, :]
             p0 = float(np.vdot(w0, w0).real)
             p1 = float(np.vdot(w1, w1).real)
-            b = 1 if rng.random() * (p0 + p1) >= p0 else 0
+            b = 1 if u[s, q] * (p0 + p1) >= p0 else 0
             w, p = (w1, p1) if b else (w0, p0)
             v = w / np.sqrt(p)
             out[s, q] = b
     return out
+
+
+def perfect_sample(mps: MPS, n_shots: int, rng: np.random.Generator) -> np.ndarray:
+    """perfect_sample_u with uniforms drawn from rng (row by row, qubit 0 first)."""
+    return perfect_sample_u(mps, rng.random((n_shots, mps.n)))

@@ -99,6 +99,7 @@ _sig("tnsim_graph_destroy", C.c_int, [_P])
 _sig("tnsim_apply_circuit", C.c_int, [_P, C.c_int32, _I32P, _I32P, _DP, _I32P, _I32P, _DP])
 _sig("tnsim_circuit_layerize", C.c_int, [C.c_int32, C.c_int32, _I32P, _I32P, _DP, C.c_int32, C.c_int32,
                                          _I32P, _I32P, _I32P, _I32P, _DP, _DP])
+_sig("tnsim_sample", C.c_int, [_P, C.c_int64, _DP, C.POINTER(C.c_uint8), _I64P])
 _sig("tnsim_last_error", C.c_char_p, [])
 _sig("tnsim_version", C.c_char_p, [])
 
@@ -111,7 +112,7 @@ def exported_symbols():
             "tnsim_amplitudes", "tnsim_expect_pauli", "tnsim_grad", "tnsim_last_stats",
             "tnsim_profile_enable", "tnsim_profile_read", "tnsim_two_site_update_noalloc",
             "tnsim_plan_create", "tnsim_plan_launch", "tnsim_plan_destroy", "tnsim_graph_create",
-            "tnsim_graph_launch", "tnsim_graph_destroy", "tnsim_apply_circuit", "tnsim_circuit_layerize",
+            "tnsim_graph_launch", "tnsim_graph_destroy", "tnsim_apply_circuit", "tnsim_circuit_layerize", "tnsim_sample",
             "tnsim_last_error", "tnsim_version"]
 
 
@@ -313,6 +314,17 @@ def tnsim_expect_pauli(h, paulis) -> np.ndarray:
     return out[: 2 * len(terms)].view(np.complex128).copy()
 
 
+def tnsim_sample(h, uniforms):
+    """Perfect sampling with the given uniforms [n_shots, n_qubits] in [0, 1);
+    returns (bits uint8 [n_shots, n_qubits], distinct prefixes evaluated)."""
+    u = np.ascontiguousarray(uniforms, dtype=np.float64)
+    assert u.ndim == 2
+    bits = np.zeros(u.shape, dtype=np.uint8)
+    nodes = C.c_int64(0)
+    _check(lib.tnsim_sample(h, u.shape[0], _dptr(u), bits.ctypes.data_as(C.POINTER(C.c_uint8)), C.byref(nodes)))
+    return bits, nodes.value
+
+
 def tnsim_grad(*args, **kwargs):
     _check(lib.tnsim_grad(None, None, 0, None, None, None, None))
 
@@ -430,6 +442,11 @@ class MPS:
 
     def apply_circuit(self, ops):
         return tnsim_apply_circuit(self.h, ops)
+
+    def sample(self, n_shots: int, seed: int = 0):
+        """n_shots bitstrings; the uniforms are drawn on the host from numpy's PCG64(seed)."""
+        u = np.random.default_rng(seed).random((int(n_shots), self.n))
+        return tnsim_sample(self.h, u)[0]
 
     def bond_dims(self):
         return tnsim_bond_dims(self.h, self.n)

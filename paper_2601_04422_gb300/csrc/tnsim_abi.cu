@@ -1223,6 +1223,87 @@ tnsim_status tnsim_expect_pauli(tnsim_mps* m, int32_t n_terms, const char* pauli
     return TNSIM_OK;
 }
 
+tnsim_status tnsim_sample(tnsim_mps* m, int64_t n_shots, const double* uniforms, uint8_t* bits_out,
+                          int64_t* n_nodes_out) {
+    if (!m) return fail(TNSIM_EINVAL, "state is NULL");
+    if (n_shots < 0 || n_shots > (int64_t)1 << 24) return fail(TNSIM_EINVAL, "n_shots must be in [0, 2^24]");
+    if (n_nodes_out) *n_nodes_out = 0;
+    if (n_shots == 0) return TNSIM_OK;
+    if (!uniforms || !bits_out) return fail(TNSIM_EINVAL, "NULL argument");
+    const int n = m->n;
+    const int64_t nu = n_shots * n;
+    for (int64_t i = 0; i < nu; ++i)
+        if (!(uniforms[i] >= 0.0 && uniforms[i] < 1.0)) return fail(TNSIM_EINVAL, "uniforms must lie in [0, 1)");
+    DevGuard g(m->device);
+    tnsim_status s = refresh_dims(m);   // exact bond dimensions on the host
+    if (s != TNSIM_OK) return s;
+    int chi_cap = 1;
+    for (int b = 0; b <= n; ++b) chi_cap = std::max(chi_cap, m->ub[b]);
+    const size_t es = m->esz, env = (size_t)chi_cap * chi_cap * es;
+    const size_t S = (size_t)n_shots;
+    cudaStream_t st = m->stream;
+    // one stream-ordered allocation for everything
+    size_t off = 0;
+    auto take = [&](size_t bytes) { const size_t o = off; off += (bytes + 255) / 256 * 256; return o; };
+    const size_t o_R = take(env * (n + 1)), o_tmp = take(env * 2), o_op = take(8 * sizeof(double));
+    const size_t o_u = take(sizeof(double) * nu), o_bits = take((size_t)nu);
+    const size_t o_v0 = take(S * chi_cap * es), o_v1 = take(S * chi_cap * es);
+    const size_t o_w = take(S * 2 * chi_cap * es), o_y = take(S * 2 * chi_cap * es);
+    const size_t o_p = take(sizeof(double) * 2 * S), o_flag = take(sizeof(int) * 2 * S);
+    const size_t o_id = take(sizeof(int) * 2 * S), o_par = take(sizeof(int) * S), o_node = take(sizeof(int) * S);
+    const size_t o_cnt = take(sizeof(int) + sizeof(unsigned long long) + 8);
+    char* base = nullptr;
+    CUDA_TRY(cudaMallocAsync((void**)&base, off, st));
+    SampleWork w;
+    w.v_cur = base + o_v0;
+    w.v_next = base + o_v1;
+    w.w = base + o_w;
+    w.y = base + o_y;
+    w.p = (double*)(base + o_p);
+    w.flag = (int*)(base + o_flag);
+    w.id = (int*)(base + o_id);
+    w.parent = (int*)(base + o_par);
+    w.node_of = (int*)(base + o_node);
+    w.nodes = (int*)(base + o_cnt);
+    w.total = (unsigned long long*)(base + o_cnt + 8);
+    const double ident[8] = {1, 0, 0, 0, 0, 0, 1, 0};
+    std::vector<char> one(es, 0);
+    if (m->dt == TNSIM_C64) { const float f = 1.0f; std::memcpy(one.data(), &f, 4); }
+    else { const double f = 1.0; std::memcpy(one.data(), &f, 8); }
+    struct Cnt { int nodes; int pad; unsigned long long total; } c0 = {1, 0, 1ull};
+    cudaError_t e = cudaMemcpyAsync(base + o_op, ident, sizeof(ident), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(base + o_u, uniforms, sizeof(double) * nu, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(base + o_R + env * n, one.data(), es, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(base + o_v0, one.data(), es, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(base + o_cnt, &c0, sizeof(c0), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(w.node_of, 0, sizeof(int) * S, st);
+    // right environments R_n = [[1]], R_q from R_{q+1} (identity operator)
+    for (int q = n - 1; q >= 1 && e == cudaSuccess; --q)
+        e = (m->dt == TNSIM_C64)
+                ? launch_transfer<float>(site_ptr(m, q), m->d_chi, q, (const double*)(base + o_op),
+                                         base + o_R + env * (q + 1), base + o_tmp, base + o_R + env * q, chi_cap, 0, st)
+                : launch_transfer<double>(site_ptr(m, q), m->d_chi, q, (const double*)(base + o_op),
+                                          base + o_R + env * (q + 1), base + o_tmp, base + o_R + env * q, chi_cap, 0, st);
+    for (int q = 0; q < n && e == cudaSuccess; ++q) {
+        const int64_t bound = q >= 40 ? n_shots : std::min<int64_t>(n_shots, (int64_t)1 << q);
+        e = (m->dt == TNSIM_C64)
+                ? launch_sample_site<float>(site_ptr(m, q), m->ub[q], m->ub[q + 1], base + o_R + env * (q + 1), q, n,
+                                            n_shots, (int)bound, (const double*)(base + o_u), (uint8_t*)(base + o_bits), w, st)
+                : launch_sample_site<double>(site_ptr(m, q), m->ub[q], m->ub[q + 1], base + o_R + env * (q + 1), q, n,
+                                             n_shots, (int)bound, (const double*)(base + o_u), (uint8_t*)(base + o_bits), w, st);
+        std::swap(w.v_cur, w.v_next);
+    }
+    Cnt c1 = {0, 0, 0ull};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(bits_out, base + o_bits, (size_t)nu, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&c1, base + o_cnt, sizeof(c1), cudaMemcpyDeviceToHost, st);
+    cudaFreeAsync(base, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail(TNSIM_ECUDA, std::string("sample: ") + cudaGetErrorString(e));
+    // prefixes evaluated: every distinct prefix of length 0 .. n-1
+    if (n_nodes_out) *n_nodes_out = (int64_t)c1.total - c1.nodes;
+    return TNSIM_OK;
+}
+
 tnsim_status tnsim_grad(const void*, const double*, int32_t, const void*, const tnsim_params*,
                         double*, double*) {
     return fail(TNSIM_EUNSUPPORTED, "tnsim_grad is not built yet");

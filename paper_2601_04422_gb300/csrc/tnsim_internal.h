@@ -116,6 +116,27 @@ cudaError_t launch_theta_tc(int mode, const GateDesc* d, int n_gates, int chiL_m
 cudaError_t encode_plane_maps(int mode, void* planes, int slots, int rows, int kstride, struct CUtensorMap_st* host_a,
                               struct CUtensorMap_st* host_b);
 
+// Work buffers of perfect sampling (k_sample.cu); node arrays hold at most `shots` entries
+struct SampleWork {
+    void* v_cur;                   // [nodes][chi_max] prefix row vectors of this site
+    void* v_next;                  // [nodes][chi_max] those of the next site
+    void* w;                       // [nodes][2 chi_max]  v A_q
+    void* y;                       // [2 nodes][chi_max]  (v A_q^b) Rt_{q+1}
+    double* p;                     // [2 nodes] outcome weights
+    int* flag;                     // [2 nodes] child (node, bit) drawn by some shot
+    int* id;                       // [2 nodes] next-site index of each child, -1 if none
+    int* parent;                   // [shots] child (2 node + bit) of each next-site node
+    int* node_of;                  // [shots] node of each shot
+    int* nodes;                    // current node count (device)
+    unsigned long long* total;     // nodes summed over sites (device)
+};
+// One site of perfect sampling: weights, draws, memoised prefix update.  node_bound
+// is a host upper bound of the current node count (min(shots, 2^q)).
+template <typename T>
+cudaError_t launch_sample_site(const void* site, int cl, int cr, const void* rt_next, int q, int n,
+                               int64_t shots, int node_bound, const double* u, uint8_t* bits,
+                               SampleWork& w, cudaStream_t s);
+
 // Set the thread-local message returned by tnsim_last_error().
 void set_last_error(const char* msg);
 
