@@ -68,6 +68,15 @@ typedef enum {
     TNSIM_GEMM_BF16X3 = 3   /* tensor cores (tcgen05 kind::f16): 3 split BF16 products, FP32 accumulate */
 } tnsim_gemm_mode;
 
+/* Form of the state that a two-qubit update maintains. */
+typedef enum {
+    TNSIM_FORM_PAPER = 0,    /* the paper's update (Sec. III.A): U to the left site, S.V^H to the right */
+    TNSIM_FORM_CANONICAL = 1 /* right-canonical sites with every bond's singular values kept beside them
+                                (Hastings form): the SVD is of diag(Lam_q) theta, whose singular values are
+                                the Schmidt coefficients of the cut, so truncation is optimal for the
+                                state; the right site becomes V^H and the left site theta.V */
+} tnsim_form;
+
 typedef struct {
     int32_t chi_max;    /* bond-dimension cap, >= 1 (Sec. II.A: truncate to a fixed chi) */
     double cutoff;      /* relative discarded-weight cutoff in [0, 1); 0 = none */
@@ -76,10 +85,11 @@ typedef struct {
     double jacobi_tol;  /* rotate a column pair while |g| > tol*sqrt(a*b); 0 = default */
     int32_t schedule;   /* tnsim_schedule */
     int32_t gemm;       /* tnsim_gemm_mode (complex64 only) */
+    int32_t form;       /* tnsim_form */
 } tnsim_params;
 
 /* Fill *out with the defaults for dtype dt (chi_max 64, cutoff 0, renormalize 1,
- * batched schedule, FP32 contraction).
+ * batched schedule, FP32 contraction, the paper's form).
  * Errors: EINVAL if out is NULL or dt unknown. */
 tnsim_status tnsim_params_default(tnsim_dtype dt, tnsim_params* out);
 
@@ -214,8 +224,10 @@ tnsim_status tnsim_bond_spectrum(tnsim_mps* m, int32_t bond, double* s_out, int3
 tnsim_status tnsim_export_sites(tnsim_mps* m, double* out, int64_t cap, int64_t* needed);
 
 /* Replace the state by host sites in the export layout; dims holds chi_0..chi_n
- * (chi_0 = chi_n = 1, chi_q within the handle's capacity).  Synchronous.
- * Errors: EINVAL (dims out of range). */
+ * (chi_0 = chi_n = 1, chi_q within the handle's capacity).  The stored bond spectra
+ * are cleared.  Synchronous.
+ * Errors: EINVAL (dims out of range), EUNSUPPORTED (a TNSIM_FORM_CANONICAL state: its
+ * bond spectra would be unknown). */
 tnsim_status tnsim_import_sites(tnsim_mps* m, const int32_t* dims, const double* data);
 
 /* <x|psi> for n_str bitstrings (bits: n_str*n_qubits bytes of 0/1, host, qubit 0

@@ -149,15 +149,56 @@ def apply_2q(mps: MPS, q: int, g: np.ndarray, chi_max: int, cutoff: float = 0.0,
     return GateRecord(q, s, k, disc, s_kept)
 
 
+def apply_2q_canonical(mps: MPS, q: int, g: np.ndarray, chi_max: int, cutoff: float = 0.0,
+                       renormalize: bool = True) -> GateRecord:
+    """Local two-qubit gate with the state kept in right-canonical form and the
+    singular values of every bond stored beside it (Hastings, "Light-cone matrix
+    product", J. Math. Phys. 50, 095207 (2009)).
+
+    With Lam the singular values of bond q (those of the last SVD there; ones for a
+    bond no SVD has touched) and theta the gate applied to the merged sites as in
+    apply_2q:
+      * the SVD is taken of diag(Lam) theta (rows (l, a) scaled by Lam[l]), whose
+        singular values are the Schmidt coefficients of the cut q+1, so truncation
+        acts on them;
+      * the right site becomes V^H (k rows), the left site theta V -- without
+        dividing by Lam -- times the renormalisation factor;
+      * bond q+1 stores the kept (renormalised) singular values.
+    """
+    a, b = mps.sites[q], mps.sites[q + 1]
+    chi_l, chi_r = a.shape[0], b.shape[2]
+    lam = mps.spectrum[q] if mps.spectrum[q] is not None else np.ones(chi_l)
+    assert lam.shape[0] == chi_l
+    theta = contract_gate(merge_sites(a, b), g)
+    mat0 = theta.reshape(2 * chi_l, 2 * chi_r)
+    mat = (lam[:, None, None, None] * theta).reshape(2 * chi_l, 2 * chi_r)
+    u, s, vh = np.linalg.svd(mat, full_matrices=False)
+    k, disc = truncation_rank(s, mat.shape[0], mat.shape[1], chi_max, cutoff)
+    s_kept = s[:k].copy()
+    scale = 1.0
+    if renormalize:
+        kept = float(np.sum(s_kept ** 2))
+        if kept > 0.0:
+            scale = np.sqrt(float(np.sum(s * s)) / kept)
+    s_kept *= scale
+    vk = vh[:k, :]
+    mps.sites[q] = (scale * (mat0 @ vk.conj().T)).reshape(chi_l, 2, k)
+    mps.sites[q + 1] = vk.reshape(k, 2, chi_r)
+    mps.spectrum[q + 1] = s_kept.copy()
+    return GateRecord(q, s, k, disc, s_kept)
+
+
 def apply_layer(mps: MPS, layer, chi_max: int, cutoff: float = 0.0,
-                renormalize: bool = True) -> List[GateRecord]:
-    """One layer: its one-qubit gates on every qubit, then its disjoint two-qubit gates."""
+                renormalize: bool = True, canonical: bool = False) -> List[GateRecord]:
+    """One layer: its one-qubit gates on every qubit, then its disjoint two-qubit gates
+    (apply_2q, or apply_2q_canonical when ``canonical``)."""
     if layer.u1 is not None:
         for q in range(mps.n):
             apply_1q(mps, q, layer.u1[q])
+    upd = apply_2q_canonical if canonical else apply_2q
     recs = []
     for q, g in zip(layer.pairs, layer.g4):
-        recs.append(apply_2q(mps, int(q), g, chi_max, cutoff, renormalize))
+        recs.append(upd(mps, int(q), g, chi_max, cutoff, renormalize))
     return recs
 
 
@@ -175,7 +216,7 @@ def reversed_pair(g: np.ndarray) -> np.ndarray:
 
 
 def apply_2q_any(mps: MPS, qa: int, qb: int, g: np.ndarray, chi_max: int, cutoff: float = 0.0,
-                 renormalize: bool = True) -> List[GateRecord]:
+                 renormalize: bool = True, canonical: bool = False) -> List[GateRecord]:
     """Two-qubit gate on any two distinct qubits by the SWAP method (Sec. III.B
     simulation_kernel: SWAP gates make the distant sites local, the gate is applied,
     and the SWAPs are reversed).  ``g`` has basis index 2*b_qa + b_qb.
@@ -187,17 +228,18 @@ def apply_2q_any(mps: MPS, qa: int, qb: int, g: np.ndarray, chi_max: int, cutoff
     if qa == qb:
         raise ValueError("the two qubits must differ")
     lo, hi, gl = (qa, qb, g) if qa < qb else (qb, qa, reversed_pair(g))
+    upd = apply_2q_canonical if canonical else apply_2q
     recs = []
     for j in range(hi - 1, lo, -1):
-        recs.append(apply_2q(mps, j, SWAP, chi_max, cutoff, renormalize))
-    recs.append(apply_2q(mps, lo, gl, chi_max, cutoff, renormalize))
+        recs.append(upd(mps, j, SWAP, chi_max, cutoff, renormalize))
+    recs.append(upd(mps, lo, gl, chi_max, cutoff, renormalize))
     for j in range(lo + 1, hi):
-        recs.append(apply_2q(mps, j, SWAP, chi_max, cutoff, renormalize))
+        recs.append(upd(mps, j, SWAP, chi_max, cutoff, renormalize))
     return recs
 
 
 def run_ops(n: int, ops, chi_max: int, cutoff: float = 0.0, renormalize: bool = True,
-            mps: Optional[MPS] = None):
+            mps: Optional[MPS] = None, canonical: bool = False):
     """Apply a gate list in program order from |0...0> (or from ``mps``).  ``ops`` holds
     (qa, qb, matrix) with qb None or negative for a one-qubit gate.  Returns
     (mps, records of every two-qubit update, SWAPs included)."""
@@ -209,16 +251,16 @@ def run_ops(n: int, ops, chi_max: int, cutoff: float = 0.0, renormalize: bool = 
         if qb is None or qb < 0:
             apply_1q(mps, int(qa), g)
         else:
-            recs += apply_2q_any(mps, int(qa), int(qb), g, chi_max, cutoff, renormalize)
+            recs += apply_2q_any(mps, int(qa), int(qb), g, chi_max, cutoff, renormalize, canonical)
     return mps, recs
 
 
 def run_circuit(circuit, chi_max: int, cutoff: float = 0.0, renormalize: bool = True,
-                mps: Optional[MPS] = None):
+                mps: Optional[MPS] = None, canonical: bool = False):
     """Run every layer from |0...0> (or from ``mps``); returns (mps, records per layer)."""
     if mps is None:
         mps = zero_state(circuit.n_qubits)
-    recs = [apply_layer(mps, layer, chi_max, cutoff, renormalize) for layer in circuit.layers]
+    recs = [apply_layer(mps, layer, chi_max, cutoff, renormalize, canonical) for layer in circuit.layers]
     return mps, recs
 
 

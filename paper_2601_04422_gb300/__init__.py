@@ -6,7 +6,7 @@ when the library has not been built -- there is no CPU fallback.
 """
 from ._abi import (  # noqa: F401
     TNSIM_C64, TNSIM_C128, TNSIM_SCHED_BATCHED, TNSIM_SCHED_PLAIN, TNSIM_GEMM_FP32, TNSIM_GEMM_FP32_3M,
-    TNSIM_GEMM_TF32X3, TNSIM_GEMM_BF16X3, TNSIM_OK, TNSIM_EINVAL,
+    TNSIM_GEMM_TF32X3, TNSIM_GEMM_BF16X3, TNSIM_FORM_PAPER, TNSIM_FORM_CANONICAL, TNSIM_OK, TNSIM_EINVAL,
     TNSIM_ENOMEM, TNSIM_ECUDA, TNSIM_ENOCONV, TNSIM_ETIMEOUT, TNSIM_EUNSUPPORTED,
     TnsimError, TnsimConvergenceWarning, lib, lib_path, exported_symbols,
     tnsim_params, tnsim_params_default, tnsim_mps_create, tnsim_mps_destroy, tnsim_apply_layer,

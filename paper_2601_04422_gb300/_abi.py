@@ -20,6 +20,7 @@ TNSIM_OK, TNSIM_EINVAL, TNSIM_ENOMEM, TNSIM_ECUDA, TNSIM_ENOCONV, TNSIM_ETIMEOUT
 TNSIM_C64, TNSIM_C128 = 0, 1
 TNSIM_SCHED_BATCHED, TNSIM_SCHED_PLAIN = 0, 1
 TNSIM_GEMM_FP32, TNSIM_GEMM_FP32_3M, TNSIM_GEMM_TF32X3, TNSIM_GEMM_BF16X3 = 0, 1, 2, 3
+TNSIM_FORM_PAPER, TNSIM_FORM_CANONICAL = 0, 1
 
 _NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOCONV", 5: "ETIMEOUT", 6: "EUNSUPPORTED"}
 
@@ -45,7 +46,7 @@ lib = C.CDLL(lib_path)
 class tnsim_params(C.Structure):
     _fields_ = [("chi_max", C.c_int32), ("cutoff", C.c_double), ("renormalize", C.c_int32),
                 ("max_sweeps", C.c_int32), ("jacobi_tol", C.c_double), ("schedule", C.c_int32),
-                ("gemm", C.c_int32)]
+                ("gemm", C.c_int32), ("form", C.c_int32)]
 
 
 _P = C.c_void_p
@@ -413,11 +414,12 @@ class MPS:
 
     def __init__(self, n_qubits: int, dtype: int = TNSIM_C64, chi_max: int = 64, cutoff: float = 0.0,
                  renormalize: bool = True, max_sweeps: int = 0, jacobi_tol: float = 0.0,
-                 schedule: int = TNSIM_SCHED_BATCHED, gemm: int = TNSIM_GEMM_FP32, stream=None):
+                 schedule: int = TNSIM_SCHED_BATCHED, gemm: int = TNSIM_GEMM_FP32, stream=None,
+                 form: int = TNSIM_FORM_PAPER):
         p = tnsim_params_default(dtype)
         p.chi_max, p.cutoff, p.renormalize = int(chi_max), float(cutoff), int(bool(renormalize))
         p.max_sweeps, p.jacobi_tol, p.schedule = int(max_sweeps), float(jacobi_tol), int(schedule)
-        p.gemm = int(gemm)
+        p.gemm, p.form = int(gemm), int(form)
         self.n = int(n_qubits)
         self.dtype = dtype
         self.params = p

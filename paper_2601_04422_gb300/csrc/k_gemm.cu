@@ -12,6 +12,7 @@
 //  k_right : the new right site S.V^H (Sec. III.A "Two Qubit Gate").  With W = theta.V
 //            and U = W.S^-1, row j of S.V^H equals u_j^H theta, so the right site is
 //            the product U_kept^H . theta0 scaled per row -- no V is accumulated.
+//            In canonical form (k_canon.cu) it is V^H of diag(Lam_q) theta instead.
 #include "tnsim_internal.h"
 
 namespace tnsim {
@@ -202,7 +203,10 @@ __global__ void __launch_bounds__(256) k_right(const GateDesc* __restrict__ gd) 
         if (j < k) {
             pj[tid] = d.perm[j];
             const double s2j = d.s2[j];
-            fj[tid] = s2j > 0.0 ? (T)(d.out->scale / sqrt(s2j)) : (T)0;
+            // paper's form: row j of S.V^H (times the renormalisation); canonical form:
+            // row j of V^H = u_j^H diag(Lam_q) theta / s_j = w_j^H diag(Lam_q) theta / s_j^2
+            if (d.canon) fj[tid] = s2j > 0.0 ? (T)(1.0 / s2j) : (T)0;
+            else fj[tid] = s2j > 0.0 ? (T)(d.out->scale / sqrt(s2j)) : (T)0;
         } else {
             pj[tid] = -1;
             fj[tid] = 0;
@@ -212,6 +216,7 @@ __global__ void __launch_bounds__(256) k_right(const GateDesc* __restrict__ gd) 
 
     const C* Wm = (const C*)d.W;
     const C* T0 = (const C*)d.theta0;
+    const int lk = d.canon ? *d.lam_k : 0;
     C acc[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
@@ -231,6 +236,11 @@ __global__ void __launch_bounds__(256) k_right(const GateDesc* __restrict__ gd) 
                 As[ld_k + e][ld_row] = v;
                 C w; w.x = 0; w.y = 0;
                 if (col_t < n && row < m) w = T0[(size_t)col_t * m + row];
+                if (d.canon && row < m && (row >> 1) < lk) {
+                    const T f = (T)d.lam[row >> 1];
+                    w.x *= f;
+                    w.y *= f;
+                }
                 Bs[ld_k + e][ld_row] = w;
             }
         }

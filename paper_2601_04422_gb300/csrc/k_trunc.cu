@@ -152,6 +152,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_left(const GateDesc* __restrict__ gd) {
     using C = typename CT<T>::type;
     const GateDesc& d = gd[blockIdx.z];
+    if (d.canon) return;   // canonical form: the left site is theta V (k_canon.cu)
     const int q = d.q;
     const int chiL = d.chi[q];
     const int m = 2 * chiL;

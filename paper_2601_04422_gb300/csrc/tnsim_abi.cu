@@ -114,6 +114,7 @@ struct tnsim_plan {
     GateOut* d_out = nullptr;
     Site1Desc* d_s1 = nullptr;
     JacobiCtl* d_ctl = nullptr;
+    bool canon = false;            // some state of the plan is in canonical form
 };
 
 struct tnsim_graph {
@@ -140,6 +141,7 @@ tnsim_status check_params(const tnsim_params* p) {
     if (p->schedule != TNSIM_SCHED_BATCHED && p->schedule != TNSIM_SCHED_PLAIN)
         return fail(TNSIM_EINVAL, "bad schedule");
     if (p->gemm < TNSIM_GEMM_FP32 || p->gemm > TNSIM_GEMM_BF16X3) return fail(TNSIM_EINVAL, "bad gemm mode");
+    if (p->form != TNSIM_FORM_PAPER && p->form != TNSIM_FORM_CANONICAL) return fail(TNSIM_EINVAL, "bad form");
     return TNSIM_OK;
 }
 
@@ -274,6 +276,9 @@ tnsim_status upload_desc(cudaStream_t st, const std::vector<GateJob>& jobs, Gate
         d.tc_slot = j.slot;
         d.tc_rows = m->tc_rows;
         d.tc_k = m->tc_k;
+        d.canon = m->p.form == TNSIM_FORM_CANONICAL ? 1 : 0;
+        d.lam = m->d_spec + (size_t)j.q * m->p.chi_max;
+        d.lam_k = m->d_spec_k + j.q;
     }
     CUDA_TRY(cudaMemcpyAsync(d_desc, h_desc, sizeof(GateDesc) * ng, cudaMemcpyHostToDevice, st));
     return TNSIM_OK;
@@ -302,6 +307,9 @@ tnsim_status launch_gates(cudaStream_t st, const std::vector<GateJob>& jobs, con
         CUDA_TRY(launch_theta_tc(pm->tc_mode, d_desc, ng, chiL_max, chiM_max, chiR_max, st));
     }
     prof_end(pm, st, TNSIM_K_THETA, ev);
+    bool canon = false;
+    for (const GateJob& j : jobs) canon = canon || j.m->p.form == TNSIM_FORM_CANONICAL;
+    if (canon) CUDA_TRY(launch_scale_rows<T>(d_desc, ng, st));
     CUDA_TRY(cudaMemsetAsync(pm->d_ctl, 0, sizeof(JacobiCtl), st));
     ev = prof_begin(pm, st);
     CUDA_TRY(launch_jacobi<T>(d_desc, ng, m_max, n_max, tol, sweeps, pm->d_ctl, st));
@@ -314,6 +322,7 @@ tnsim_status launch_gates(cudaStream_t st, const std::vector<GateJob>& jobs, con
     prof_end(pm, st, TNSIM_K_LEFT, ev);
     ev = prof_begin(pm, st);
     CUDA_TRY(launch_right<T>(d_desc, ng, k_max, n_max, st));
+    if (canon) CUDA_TRY(launch_left_canon<T>(d_desc, ng, m_max, k_max, st));
     prof_end(pm, st, TNSIM_K_RIGHT, ev);
     // bounds for the next layer
     for (const GateJob& j : jobs) {
@@ -432,6 +441,7 @@ tnsim_status tnsim_params_default(tnsim_dtype dt, tnsim_params* out) {
     out->jacobi_tol = 0.0;
     out->schedule = TNSIM_SCHED_BATCHED;
     out->gemm = TNSIM_GEMM_FP32;
+    out->form = TNSIM_FORM_PAPER;
     return TNSIM_OK;
 }
 
@@ -864,6 +874,7 @@ tnsim_status tnsim_plan_create(tnsim_mps* const* ms, int32_t n_states, const int
     p->device = m0->device;
     p->dt = m0->dt;
     p->gemm = m0->p.gemm;
+    for (int i = 0; i < n_states; ++i) p->canon = p->canon || ms[i]->p.form == TNSIM_FORM_CANONICAL;
     p->tc_mode = m0->tc_mode;
     p->tol = m0->p.jacobi_tol;
     std::vector<GateJob> jobs;
@@ -947,18 +958,22 @@ tnsim_status tnsim_plan_launch(tnsim_plan* p) {
     const int m_max = 2 * p->chiL_max, n_max = 2 * p->chiR_max;
     if (p->dt == TNSIM_C128) {
         CUDA_TRY(launch_theta<double>(p->d_desc, ng, p->chiL_max, p->chiR_max, st));
+        if (p->canon) CUDA_TRY(launch_scale_rows<double>(p->d_desc, ng, st));
         CUDA_TRY(launch_jacobi<double>(p->d_desc, ng, m_max, n_max, p->tol, p->sweeps, p->d_ctl, st));
         CUDA_TRY(launch_truncate<double>(p->d_desc, ng, st));
         CUDA_TRY(launch_left<double>(p->d_desc, ng, m_max, p->k_max, st));
         CUDA_TRY(launch_right<double>(p->d_desc, ng, p->k_max, n_max, st));
+        if (p->canon) CUDA_TRY(launch_left_canon<double>(p->d_desc, ng, m_max, p->k_max, st));
     } else {
         if (p->gemm == TNSIM_GEMM_FP32) CUDA_TRY(launch_theta<float>(p->d_desc, ng, p->chiL_max, p->chiR_max, st));
         else if (p->gemm == TNSIM_GEMM_FP32_3M) CUDA_TRY(launch_theta_3m(p->d_desc, ng, p->chiL_max, p->chiR_max, st));
         else CUDA_TRY(launch_theta_tc(p->tc_mode, p->d_desc, ng, p->chiL_max, p->chiM_max, p->chiR_max, st));
+        if (p->canon) CUDA_TRY(launch_scale_rows<float>(p->d_desc, ng, st));
         CUDA_TRY(launch_jacobi<float>(p->d_desc, ng, m_max, n_max, p->tol, p->sweeps, p->d_ctl, st));
         CUDA_TRY(launch_truncate<float>(p->d_desc, ng, st));
         CUDA_TRY(launch_left<float>(p->d_desc, ng, m_max, p->k_max, st));
         CUDA_TRY(launch_right<float>(p->d_desc, ng, p->k_max, n_max, st));
+        if (p->canon) CUDA_TRY(launch_left_canon<float>(p->d_desc, ng, m_max, p->k_max, st));
     }
     // the bond upper bounds the host keeps become the capacities
     for (tnsim_mps* m : p->states)
@@ -1090,6 +1105,8 @@ tnsim_status tnsim_export_sites(tnsim_mps* m, double* out, int64_t cap, int64_t*
 
 tnsim_status tnsim_import_sites(tnsim_mps* m, const int32_t* dims, const double* data) {
     if (!m || !dims || !data) return fail(TNSIM_EINVAL, "NULL argument");
+    if (m->p.form == TNSIM_FORM_CANONICAL)
+        return fail(TNSIM_EUNSUPPORTED, "importing sites into a canonical-form state (its bond spectra are unknown)");
     if (dims[0] != 1 || dims[m->n] != 1) return fail(TNSIM_EINVAL, "terminal bonds must be 1");
     for (int b = 1; b < m->n; ++b)
         if (dims[b] < 1 || dims[b] > m->cap[b]) return fail(TNSIM_EINVAL, "bond dimension exceeds capacity");

@@ -67,6 +67,11 @@ struct GateDesc {
     int tc_slot;          // this gate's slot in the plane buffer
     int tc_rows;          // rows of every plane (2 * capmax)
     int tc_k;             // K stride of every plane (capmax rounded up to 64)
+    // canonical (Hastings) form: the SVD operand is diag(Lam_q) theta, the right site
+    // becomes V^H and the left site theta V (k_canon.cu); 0 = the paper's form
+    int canon;
+    const double* lam;    // singular values of bond q (the state's spectrum of bond q)
+    const int* lam_k;     // their count (0 = bond never decomposed: all ones)
 };
 
 // One-qubit update of one site (Eq. 3).
@@ -91,6 +96,12 @@ template <typename T>
 cudaError_t launch_left(const GateDesc* d, int n_gates, int m_max, int k_max, cudaStream_t s);
 template <typename T>
 cudaError_t launch_right(const GateDesc* d, int n_gates, int k_max, int n_max, cudaStream_t s);
+// Canonical form: scale W's rows by Lam_q (and recompute |W|_F^2); re-orthonormalise the
+// new right site's rows and form the left site theta V.
+template <typename T>
+cudaError_t launch_scale_rows(const GateDesc* d, int n_gates, cudaStream_t s);
+template <typename T>
+cudaError_t launch_left_canon(const GateDesc* d, int n_gates, int m_max, int k_max, cudaStream_t s);
 template <typename T>
 cudaError_t launch_site1q(const Site1Desc* d, int n_sites, int cap_lr, cudaStream_t s);
 

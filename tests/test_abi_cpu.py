@@ -40,17 +40,19 @@ def test_every_declared_symbol_is_exported(T):
 
 def test_params_default_and_version(T):
     p = T.tnsim_params_default(T.TNSIM_C64)
-    assert p.chi_max == 64 and p.cutoff == 0.0 and p.renormalize == 1 and p.schedule == 0
+    assert p.chi_max == 64 and p.cutoff == 0.0 and p.renormalize == 1 and p.schedule == 0 and p.form == 0
     assert "sm_103a" in T.tnsim_version()
     with pytest.raises(T.TnsimError):
         T.tnsim_params_default(7)
 
 
 def test_params_struct_layout_matches_header(T):
-    # offsets of the C struct (int32, double, int32, int32, double, int32) with natural alignment
+    # offsets of the C struct (int32, double, int32, int32, double, int32, int32, int32) with
+    # natural alignment
     P = T.tnsim_params
     assert P.cutoff.offset == 8 and P.renormalize.offset == 16 and P.max_sweeps.offset == 20
-    assert P.jacobi_tol.offset == 24 and P.schedule.offset == 32 and ctypes.sizeof(P) == 40
+    assert P.jacobi_tol.offset == 24 and P.schedule.offset == 32 and P.gemm.offset == 36
+    assert P.form.offset == 40 and ctypes.sizeof(P) == 48
 
 
 def test_library_is_sm103a_only():
