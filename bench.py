@@ -256,6 +256,9 @@ def run_ours(args, world, rank, local):
         layer_dev(i)
     m.sync()
     dims = m.bond_dims()
+    # autotuner: time the Jacobi launch configurations on the first timed layer's gates
+    tune_choice, tune_ms = T.tnsim_autotune(m.h, circ.layers[PRESAT + args.warmup].pairs,
+                                            circ.layers[PRESAT + args.warmup].g4, reps=2)
     T.tnsim_last_stats(m.h)
     T.tnsim_profile_read(m.h)
 
@@ -419,6 +422,8 @@ def run_ours(args, world, rank, local):
         cfg["gates_per_step"] = gates_all / args.steps
         cfg["parallelism"] = f"replicas x{world}" if world > 1 else "single GPU"
         cfg["jacobi_sweeps_per_gate"] = stats["sweeps"] / max(stats["gates"], 1)
+        cfg["jacobi_config"] = {"chosen": int(tune_choice), "autotune_ms": [float(x) for x in tune_ms],
+                                "configs": ["16-column blocks, 1 CTA/SM", "8-column blocks, 2 CTAs/SM"]}
         cfg["interior_chi"] = int(np.max(dims))
         cfg["contraction"] = {"fp32": "FP32 FMA (4M)", "fp32_3m": "FP32 FMA (3M)",
                               "tf32x3": "tcgen05 3xTF32, FP32 accumulate",

@@ -259,6 +259,26 @@ tnsim_status tnsim_expect_pauli(tnsim_mps* m, int32_t n_terms, const char* pauli
 tnsim_status tnsim_sample(tnsim_mps* m, int64_t n_shots, const double* uniforms, uint8_t* bits_out,
                           int64_t* n_nodes_out);
 
+/* Launch configurations of the Jacobi SVD: 0 -- 16-column blocks (8 for complex128
+ * at chi > 128), one persistent CTA per SM; 1 -- half-width blocks, two CTAs per SM
+ * (barriers of the two CTAs are independent; a sweep has twice the rounds). */
+#define TNSIM_JACOBI_CONFIGS 2
+
+/* Use Jacobi configuration cfg (0 or 1) for the later launches of m.
+ * Errors: EINVAL. */
+tnsim_status tnsim_set_jacobi_config(tnsim_mps* m, int32_t cfg);
+
+/* Autotuner of the Jacobi SVD: contract the given layer (n2 >= 1 pairs q, gates
+ * g4x4 on the host, as in tnsim_apply_layer) of the current state into the work
+ * space, then time the persistent Jacobi launch of that layer in every
+ * configuration (CUDA events on m's stream; W and the gate records are restored
+ * before each launch; the best of reps runs is kept), pick the fastest for m's
+ * later launches and report it in *choice_out (may be NULL); ms_out (may be NULL)
+ * receives TNSIM_JACOBI_CONFIGS times in milliseconds.  The state is not changed.
+ * Synchronous.  Errors: EINVAL (bad layer, reps outside [1, 100]), ECUDA. */
+tnsim_status tnsim_autotune(tnsim_mps* m, int32_t n2, const int32_t* q, const double* g4x4, int32_t reps,
+                            int32_t* choice_out, double* ms_out);
+
 /* Gradient of an energy with respect to gate angles: not in this build
  * (returns EUNSUPPORTED). All pointer arguments are ignored. */
 tnsim_status tnsim_grad(const void* circuit, const double* theta, int32_t n_theta,

@@ -16,6 +16,6 @@ from ._abi import (  # noqa: F401
     tnsim_stats, tnsim_profile_enable, tnsim_profile_read, TNSIM_K_NAMES,
     tnsim_two_site_update_noalloc, tnsim_plan_create, tnsim_plan_launch, tnsim_plan_destroy,
     tnsim_graph_create, tnsim_graph_launch, tnsim_graph_destroy, tnsim_apply_circuit,
-    tnsim_circuit_layerize, tnsim_sample,
+    tnsim_circuit_layerize, tnsim_sample, tnsim_set_jacobi_config, tnsim_autotune, TNSIM_JACOBI_CONFIGS,
     MPS,
 )

@@ -101,6 +101,8 @@ _sig("tnsim_apply_circuit", C.c_int, [_P, C.c_int32, _I32P, _I32P, _DP, _I32P, _
 _sig("tnsim_circuit_layerize", C.c_int, [C.c_int32, C.c_int32, _I32P, _I32P, _DP, C.c_int32, C.c_int32,
                                          _I32P, _I32P, _I32P, _I32P, _DP, _DP])
 _sig("tnsim_sample", C.c_int, [_P, C.c_int64, _DP, C.POINTER(C.c_uint8), _I64P])
+_sig("tnsim_set_jacobi_config", C.c_int, [_P, C.c_int32])
+_sig("tnsim_autotune", C.c_int, [_P, C.c_int32, _I32P, _DP, C.c_int32, _I32P, _DP])
 _sig("tnsim_last_error", C.c_char_p, [])
 _sig("tnsim_version", C.c_char_p, [])
 
@@ -113,7 +115,8 @@ def exported_symbols():
             "tnsim_amplitudes", "tnsim_expect_pauli", "tnsim_grad", "tnsim_last_stats",
             "tnsim_profile_enable", "tnsim_profile_read", "tnsim_two_site_update_noalloc",
             "tnsim_plan_create", "tnsim_plan_launch", "tnsim_plan_destroy", "tnsim_graph_create",
-            "tnsim_graph_launch", "tnsim_graph_destroy", "tnsim_apply_circuit", "tnsim_circuit_layerize", "tnsim_sample",
+            "tnsim_graph_launch", "tnsim_graph_destroy", "tnsim_apply_circuit", "tnsim_circuit_layerize", "tnsim_sample", "tnsim_set_jacobi_config",
+            "tnsim_autotune",
             "tnsim_last_error", "tnsim_version"]
 
 
@@ -324,6 +327,24 @@ def tnsim_sample(h, uniforms):
     nodes = C.c_int64(0)
     _check(lib.tnsim_sample(h, u.shape[0], _dptr(u), bits.ctypes.data_as(C.POINTER(C.c_uint8)), C.byref(nodes)))
     return bits, nodes.value
+
+
+TNSIM_JACOBI_CONFIGS = 2
+
+
+def tnsim_set_jacobi_config(h, cfg: int):
+    _check(lib.tnsim_set_jacobi_config(h, int(cfg)))
+
+
+def tnsim_autotune(h, q, g4x4, reps: int = 3):
+    """Time every Jacobi configuration on one layer; returns (choice, ms per configuration)."""
+    q = np.ascontiguousarray(q, dtype=np.int32).reshape(-1)
+    g = _cplx(g4x4, (4, 4))
+    choice = C.c_int32(0)
+    ms = np.zeros(TNSIM_JACOBI_CONFIGS, dtype=np.float64)
+    _check(lib.tnsim_autotune(h, q.shape[0], q.ctypes.data_as(_I32P), _dptr(g.view(np.float64)), int(reps),
+                              C.byref(choice), _dptr(ms)))
+    return choice.value, ms
 
 
 def tnsim_grad(*args, **kwargs):

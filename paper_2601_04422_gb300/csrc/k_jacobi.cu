@@ -254,8 +254,8 @@ constexpr int kScanTable = 2048;              // gates whose visit count is cach
 // of a sweep, decides convergence).  Gates are scanned in descriptor order, which
 // the host sorts by decreasing size.  A CTA never waits while holding a claim, so
 // a CTA with nothing to claim only waits for work that running CTAs are doing.
-template <typename T, int BC, int RPL>
-__global__ void __launch_bounds__(BC * 32, 1)
+template <typename T, int BC, int RPL, int MINB>
+__global__ void __launch_bounds__(BC * 32, MINB)
 k_jacobi(const GateDesc* __restrict__ gd, int n_gates, double tol_in, int max_sweeps,
          JacobiCtl* __restrict__ ctl) {
     using C = typename CT<T>::type;
@@ -470,18 +470,18 @@ k_jacobi(const GateDesc* __restrict__ gd, int n_gates, double tol_in, int max_sw
     }
 }
 
-template <typename T, int BC, int RPL>
+template <typename T, int BC, int RPL, int MINB>
 static cudaError_t launch_bc(const GateDesc* d, int n_gates, int m_max, int n_max, double tol,
                              int max_sweeps, JacobiCtl* ctl, cudaStream_t s) {
     using C = typename CT<T>::type;
     const size_t smem = (size_t)2 * BC * m_max * sizeof(C);
-    cudaError_t e = cudaFuncSetAttribute(k_jacobi<T, BC, RPL>,
+    cudaError_t e = cudaFuncSetAttribute(k_jacobi<T, BC, RPL, MINB>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi<T, BC, RPL>, BC * 32, smem)) !=
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi<T, BC, RPL, MINB>, BC * 32, smem)) !=
         cudaSuccess)
         return e;
     if (per_sm < 1) return cudaErrorLaunchOutOfResources;
@@ -491,29 +491,35 @@ static cudaError_t launch_bc(const GateDesc* d, int n_gates, int m_max, int n_ma
     long long grid = (long long)sms * per_sm;
     if (grid > visits) grid = visits;
     if (grid < 1) grid = 1;
-    k_jacobi<T, BC, RPL><<<(unsigned)grid, BC * 32, smem, s>>>(d, n_gates, tol, max_sweeps < 1 ? 1 : max_sweeps, ctl);
+    k_jacobi<T, BC, RPL, MINB><<<(unsigned)grid, BC * 32, smem, s>>>(d, n_gates, tol, max_sweeps < 1 ? 1 : max_sweeps, ctl);
     return cudaGetLastError();
 }
 
 // Block width BC and rows per lane RPL (= ceil(m_max / 32)) per precision: the two
-// staged blocks take 2 BC m_max elements of shared memory (at most 128 KB).
+// staged blocks take 2 BC m_max elements of shared memory (at most 128 KB).  Two
+// configurations per shape: cfg 0 -- wide blocks, one CTA per SM (fewer rounds per
+// sweep); cfg 1 -- half-width blocks, two CTAs per SM (independent barriers, twice
+// the rounds).  tnsim_autotune times both on a real layer.
 template <typename T>
 cudaError_t launch_jacobi(const GateDesc* d, int n_gates, int m_max, int n_max, double tol,
-                          int max_sweeps, JacobiCtl* ctl, cudaStream_t s) {
+                          int max_sweeps, JacobiCtl* ctl, cudaStream_t s, int cfg) {
     if (n_gates <= 0) return cudaSuccess;
-    if (m_max <= 64) return launch_bc<T, 16, 2>(d, n_gates, m_max, n_max, tol, max_sweeps, ctl, s);
-    if (m_max <= 128) return launch_bc<T, 16, 4>(d, n_gates, m_max, n_max, tol, max_sweeps, ctl, s);
-    if (m_max <= 256) return launch_bc<T, 16, 8>(d, n_gates, m_max, n_max, tol, max_sweeps, ctl, s);
+    const bool narrow = cfg == 1;
+#define TNSIM_JAC(BC, RPL, MINB) launch_bc<T, BC, RPL, MINB>(d, n_gates, m_max, n_max, tol, max_sweeps, ctl, s)
+    if (m_max <= 64) return narrow ? TNSIM_JAC(8, 2, 2) : TNSIM_JAC(16, 2, 1);
+    if (m_max <= 128) return narrow ? TNSIM_JAC(8, 4, 2) : TNSIM_JAC(16, 4, 1);
+    if (m_max <= 256) return narrow ? TNSIM_JAC(8, 8, 2) : TNSIM_JAC(16, 8, 1);
     if constexpr (sizeof(T) == 4) {
-        if (m_max <= 512) return launch_bc<T, 16, 16>(d, n_gates, m_max, n_max, tol, max_sweeps, ctl, s);
-        return launch_bc<T, 8, 32>(d, n_gates, m_max, n_max, tol, max_sweeps, ctl, s);
+        if (m_max <= 512) return narrow ? TNSIM_JAC(8, 16, 2) : TNSIM_JAC(16, 16, 1);
+        return TNSIM_JAC(8, 32, 1);
     } else {
-        if (m_max <= 512) return launch_bc<T, 8, 16>(d, n_gates, m_max, n_max, tol, max_sweeps, ctl, s);
-        return launch_bc<T, 4, 32>(d, n_gates, m_max, n_max, tol, max_sweeps, ctl, s);
+        if (m_max <= 512) return narrow ? TNSIM_JAC(4, 16, 2) : TNSIM_JAC(8, 16, 1);
+        return TNSIM_JAC(4, 32, 1);
     }
+#undef TNSIM_JAC
 }
 
-template cudaError_t launch_jacobi<float>(const GateDesc*, int, int, int, double, int, JacobiCtl*, cudaStream_t);
-template cudaError_t launch_jacobi<double>(const GateDesc*, int, int, int, double, int, JacobiCtl*, cudaStream_t);
+template cudaError_t launch_jacobi<float>(const GateDesc*, int, int, int, double, int, JacobiCtl*, cudaStream_t, int);
+template cudaError_t launch_jacobi<double>(const GateDesc*, int, int, int, double, int, JacobiCtl*, cudaStream_t, int);
 
 }  // namespace tnsim

@@ -84,6 +84,7 @@ struct tnsim_mps {
     int* d_sticky = nullptr;
     unsigned long long* d_stats = nullptr;   // 8 counters (tnsim_stats)
     JacobiCtl* d_ctl = nullptr;    // control word of the persistent Jacobi launch
+    int jac_cfg = 0;               // Jacobi launch configuration (tnsim_set_jacobi_config / tnsim_autotune)
     // tensor-core contraction (complex64 with gemm TF32X3 / BF16X3)
     int tc_mode = -1;              // -1 none, 0 TF32 planes, 1 BF16 planes
     void* d_planes = nullptr;      // [G * 8][tc_rows][tc_k] plane buffer
@@ -115,6 +116,7 @@ struct tnsim_plan {
     Site1Desc* d_s1 = nullptr;
     JacobiCtl* d_ctl = nullptr;
     bool canon = false;            // some state of the plan is in canonical form
+    int jac_cfg = 0;               // Jacobi launch configuration of the first state
 };
 
 struct tnsim_graph {
@@ -312,7 +314,7 @@ tnsim_status launch_gates(cudaStream_t st, const std::vector<GateJob>& jobs, con
     if (canon) CUDA_TRY(launch_scale_rows<T>(d_desc, ng, st));
     CUDA_TRY(cudaMemsetAsync(pm->d_ctl, 0, sizeof(JacobiCtl), st));
     ev = prof_begin(pm, st);
-    CUDA_TRY(launch_jacobi<T>(d_desc, ng, m_max, n_max, tol, sweeps, pm->d_ctl, st));
+    CUDA_TRY(launch_jacobi<T>(d_desc, ng, m_max, n_max, tol, sweeps, pm->d_ctl, st, pm->jac_cfg));
     prof_end(pm, st, TNSIM_K_JACOBI, ev);
     ev = prof_begin(pm, st);
     CUDA_TRY(launch_truncate<T>(d_desc, ng, st));
@@ -362,15 +364,10 @@ tnsim_status launch_unpaired(tnsim_mps* m, Staging* stg, int n2, const int32_t* 
     return TNSIM_OK;
 }
 
-// Enqueue one layer whose gate data is in device memory.
-tnsim_status enqueue_layer(tnsim_mps* m, Staging* stg, int n2, const int32_t* q, const double* g4_dev,
-                           const double* u1_dev, double* eps_dev) {
-    cudaStream_t st = m->stream;
-    if (u1_dev) {
-        tnsim_status s = launch_unpaired(m, stg, n2, q, u1_dev);
-        if (s != TNSIM_OK) return s;
-    }
-    if (n2 == 0) return TNSIM_OK;
+// The gates of one layer of m as jobs (slot i for pair i), largest first: the
+// persistent Jacobi kernel serves gates in descriptor order.
+std::vector<GateJob> layer_jobs(tnsim_mps* m, int n2, const int32_t* q, const double* g4_dev,
+                                const double* u1_dev, double* eps_dev) {
     std::vector<GateJob> jobs(n2);
     for (int i = 0; i < n2; ++i) {
         jobs[i].m = m;
@@ -381,12 +378,24 @@ tnsim_status enqueue_layer(tnsim_mps* m, Staging* stg, int n2, const int32_t* q,
         jobs[i].uR = u1_dev ? u1_dev + (size_t)(q[i] + 1) * 8 : nullptr;
         jobs[i].eps_dev = eps_dev ? eps_dev + i : nullptr;
     }
-    // largest gates first: the persistent Jacobi kernel serves gates in this order
     std::stable_sort(jobs.begin(), jobs.end(), [](const GateJob& a, const GateJob& b) {
         const double ca = (double)a.m->ub[a.q] * a.m->ub[a.q + 2] * a.m->ub[a.q + 2];
         const double cb = (double)b.m->ub[b.q] * b.m->ub[b.q + 2] * b.m->ub[b.q + 2];
         return ca > cb;
     });
+    return jobs;
+}
+
+// Enqueue one layer whose gate data is in device memory.
+tnsim_status enqueue_layer(tnsim_mps* m, Staging* stg, int n2, const int32_t* q, const double* g4_dev,
+                           const double* u1_dev, double* eps_dev) {
+    cudaStream_t st = m->stream;
+    if (u1_dev) {
+        tnsim_status s = launch_unpaired(m, stg, n2, q, u1_dev);
+        if (s != TNSIM_OK) return s;
+    }
+    if (n2 == 0) return TNSIM_OK;
+    std::vector<GateJob> jobs = layer_jobs(m, n2, q, g4_dev, u1_dev, eps_dev);
     CUDA_TRY(cudaMemsetAsync(m->d_out, 0, sizeof(GateOut) * n2, st));
     const double tol = default_tol(m);
     const int sweeps = default_sweeps(m);
@@ -875,6 +884,7 @@ tnsim_status tnsim_plan_create(tnsim_mps* const* ms, int32_t n_states, const int
     p->dt = m0->dt;
     p->gemm = m0->p.gemm;
     for (int i = 0; i < n_states; ++i) p->canon = p->canon || ms[i]->p.form == TNSIM_FORM_CANONICAL;
+    p->jac_cfg = m0->jac_cfg;
     p->tc_mode = m0->tc_mode;
     p->tol = m0->p.jacobi_tol;
     std::vector<GateJob> jobs;
@@ -959,7 +969,7 @@ tnsim_status tnsim_plan_launch(tnsim_plan* p) {
     if (p->dt == TNSIM_C128) {
         CUDA_TRY(launch_theta<double>(p->d_desc, ng, p->chiL_max, p->chiR_max, st));
         if (p->canon) CUDA_TRY(launch_scale_rows<double>(p->d_desc, ng, st));
-        CUDA_TRY(launch_jacobi<double>(p->d_desc, ng, m_max, n_max, p->tol, p->sweeps, p->d_ctl, st));
+        CUDA_TRY(launch_jacobi<double>(p->d_desc, ng, m_max, n_max, p->tol, p->sweeps, p->d_ctl, st, p->jac_cfg));
         CUDA_TRY(launch_truncate<double>(p->d_desc, ng, st));
         CUDA_TRY(launch_left<double>(p->d_desc, ng, m_max, p->k_max, st));
         CUDA_TRY(launch_right<double>(p->d_desc, ng, p->k_max, n_max, st));
@@ -969,7 +979,7 @@ tnsim_status tnsim_plan_launch(tnsim_plan* p) {
         else if (p->gemm == TNSIM_GEMM_FP32_3M) CUDA_TRY(launch_theta_3m(p->d_desc, ng, p->chiL_max, p->chiR_max, st));
         else CUDA_TRY(launch_theta_tc(p->tc_mode, p->d_desc, ng, p->chiL_max, p->chiM_max, p->chiR_max, st));
         if (p->canon) CUDA_TRY(launch_scale_rows<float>(p->d_desc, ng, st));
-        CUDA_TRY(launch_jacobi<float>(p->d_desc, ng, m_max, n_max, p->tol, p->sweeps, p->d_ctl, st));
+        CUDA_TRY(launch_jacobi<float>(p->d_desc, ng, m_max, n_max, p->tol, p->sweeps, p->d_ctl, st, p->jac_cfg));
         CUDA_TRY(launch_truncate<float>(p->d_desc, ng, st));
         CUDA_TRY(launch_left<float>(p->d_desc, ng, m_max, p->k_max, st));
         CUDA_TRY(launch_right<float>(p->d_desc, ng, p->k_max, n_max, st));
@@ -1318,6 +1328,100 @@ tnsim_status tnsim_sample(tnsim_mps* m, int64_t n_shots, const double* uniforms,
     if (e != cudaSuccess) return fail(TNSIM_ECUDA, std::string("sample: ") + cudaGetErrorString(e));
     // prefixes evaluated: every distinct prefix of length 0 .. n-1
     if (n_nodes_out) *n_nodes_out = (int64_t)c1.total - c1.nodes;
+    return TNSIM_OK;
+}
+
+tnsim_status tnsim_set_jacobi_config(tnsim_mps* m, int32_t cfg) {
+    if (!m) return fail(TNSIM_EINVAL, "state is NULL");
+    if (cfg < 0 || cfg >= kJacobiConfigs) return fail(TNSIM_EINVAL, "unknown Jacobi configuration");
+    m->jac_cfg = cfg;
+    return TNSIM_OK;
+}
+
+tnsim_status tnsim_autotune(tnsim_mps* m, int32_t n2, const int32_t* q, const double* g4x4, int32_t reps,
+                            int32_t* choice_out, double* ms_out) {
+    if (!m) return fail(TNSIM_EINVAL, "state is NULL");
+    if (n2 < 1) return fail(TNSIM_EINVAL, "the tuning layer needs at least one gate");
+    if (reps < 1 || reps > 100) return fail(TNSIM_EINVAL, "reps must be in [1, 100]");
+    DevGuard g(m->device);
+    tnsim_status s = check_pairs(m, n2, q);
+    if (s != TNSIM_OK) return s;
+    if (!g4x4 || !finite_all(g4x4, (size_t)n2 * 32)) return fail(TNSIM_EINVAL, "bad gate data");
+    s = refresh_dims(m);   // exact bond dimensions: the tuned launches match real ones
+    if (s != TNSIM_OK) return s;
+    cudaStream_t st = m->stream;
+    Staging* stg = acquire_staging(m);
+    std::memcpy(stg->gates, g4x4, sizeof(double) * 32 * n2);
+    CUDA_TRY(cudaMemcpyAsync(m->d_gates, stg->gates, sizeof(double) * 32 * n2, cudaMemcpyHostToDevice, st));
+    std::vector<GateJob> jobs = layer_jobs(m, n2, q, m->d_gates, nullptr, nullptr);
+    CUDA_TRY(cudaMemsetAsync(m->d_out, 0, sizeof(GateOut) * n2, st));
+    s = upload_desc(st, jobs, stg->desc, m->d_desc, nullptr);
+    CUDA_TRY(cudaEventRecord(stg->done, st));
+    if (s != TNSIM_OK) return s;
+    int chiL_max = 1, chiM_max = 1, chiR_max = 1;
+    for (const GateJob& j : jobs) {
+        chiL_max = std::max(chiL_max, m->ub[j.q]);
+        chiM_max = std::max(chiM_max, m->ub[j.q + 1]);
+        chiR_max = std::max(chiR_max, m->ub[j.q + 2]);
+    }
+    const int m_max = 2 * chiL_max, n_max = 2 * chiR_max;
+    // theta of every gate into the workspace (the sites are not touched)
+    if (m->dt == TNSIM_C128 || m->p.gemm == TNSIM_GEMM_FP32) {
+        CUDA_TRY(m->dt == TNSIM_C64 ? launch_theta<float>(m->d_desc, n2, chiL_max, chiR_max, st)
+                                    : launch_theta<double>(m->d_desc, n2, chiL_max, chiR_max, st));
+    } else if (m->p.gemm == TNSIM_GEMM_FP32_3M) {
+        CUDA_TRY(launch_theta_3m(m->d_desc, n2, chiL_max, chiR_max, st));
+    } else {
+        CUDA_TRY(launch_theta_tc(m->tc_mode, m->d_desc, n2, chiL_max, chiM_max, chiR_max, st));
+    }
+    if (m->p.form == TNSIM_FORM_CANONICAL)
+        CUDA_TRY(m->dt == TNSIM_C64 ? launch_scale_rows<float>(m->d_desc, n2, st)
+                                    : launch_scale_rows<double>(m->d_desc, n2, st));
+    // keep W and the gate records, restored before every timed launch
+    const size_t wbytes = m->ws_elems * m->esz;
+    char* bak = nullptr;
+    CUDA_TRY(cudaMallocAsync((void**)&bak, (size_t)n2 * wbytes + sizeof(GateOut) * n2, st));
+    for (int i = 0; i < n2; ++i)
+        CUDA_TRY(cudaMemcpyAsync(bak + (size_t)i * wbytes, m->d_ws + ((size_t)i * 2 + 1) * wbytes, wbytes,
+                                 cudaMemcpyDeviceToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(bak + (size_t)n2 * wbytes, m->d_out, sizeof(GateOut) * n2, cudaMemcpyDeviceToDevice, st));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    double best_ms = 0.0;
+    int best = 0;
+    cudaError_t e = cudaSuccess;
+    for (int c = 0; c < kJacobiConfigs && e == cudaSuccess; ++c) {
+        double cmin = 0.0;
+        for (int r = 0; r < reps && e == cudaSuccess; ++r) {
+            for (int i = 0; i < n2 && e == cudaSuccess; ++i)
+                e = cudaMemcpyAsync(m->d_ws + ((size_t)i * 2 + 1) * wbytes, bak + (size_t)i * wbytes, wbytes,
+                                    cudaMemcpyDeviceToDevice, st);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(m->d_out, bak + (size_t)n2 * wbytes, sizeof(GateOut) * n2,
+                                    cudaMemcpyDeviceToDevice, st);
+            if (e == cudaSuccess) e = cudaMemsetAsync(m->d_ctl, 0, sizeof(JacobiCtl), st);
+            if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+            if (e == cudaSuccess)
+                e = m->dt == TNSIM_C64
+                        ? launch_jacobi<float>(m->d_desc, n2, m_max, n_max, default_tol(m), default_sweeps(m), m->d_ctl, st, c)
+                        : launch_jacobi<double>(m->d_desc, n2, m_max, n_max, default_tol(m), default_sweeps(m), m->d_ctl, st, c);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e == cudaSuccess && (r == 0 || ms < cmin)) cmin = ms;
+        }
+        if (ms_out) ms_out[c] = cmin;
+        if (c == 0 || cmin < best_ms) { best_ms = cmin; best = c; }
+    }
+    cudaFreeAsync(bak, st);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail(TNSIM_ECUDA, std::string("autotune: ") + cudaGetErrorString(e));
+    m->jac_cfg = best;
+    if (choice_out) *choice_out = best;
     return TNSIM_OK;
 }
 

@@ -87,9 +87,12 @@ struct Site1Desc {
 template <typename T>
 cudaError_t launch_theta(const GateDesc* d, int n_gates, int chiL_max, int chiR_max,
                          cudaStream_t s);
+// cfg selects the block width / CTAs per SM (0: wide blocks, 1 CTA per SM; 1: half-width
+// blocks, 2 CTAs per SM); kJacobiConfigs of them.
+constexpr int kJacobiConfigs = 2;
 template <typename T>
 cudaError_t launch_jacobi(const GateDesc* d, int n_gates, int m_max, int n_max, double tol,
-                          int max_sweeps, JacobiCtl* ctl, cudaStream_t s);
+                          int max_sweeps, JacobiCtl* ctl, cudaStream_t s, int cfg = 0);
 template <typename T>
 cudaError_t launch_truncate(const GateDesc* d, int n_gates, cudaStream_t s);
 template <typename T>
