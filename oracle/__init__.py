@@ -12,6 +12,9 @@ mps    -- the MPS simulator (Eq. 2 state, Eq. 3 one-qubit gates, the merge /
           expectations, overlaps, canonical forms, perfect sampling).
 dense  -- a direct state-vector simulator (the full contraction of Eq. 1), used
           to pin ``mps`` on small qubit counts where nothing is truncated.
+grad   -- the reverse-mode gradient of an energy through the layered simulation
+          (the exact derivative of the truncated updates), pinned by finite
+          differences of the dense and of the truncated energies.
 
 Every function is complex128 / float64.  The singular value decomposition step
 calls LAPACK through ``numpy.linalg.svd`` (a library primitive).
@@ -22,4 +25,4 @@ designed spectra -- except the truncated regime at a degenerate cut, where the
 kept subspace is not unique ("parity unpinned": only singular values and
 discarded weights are compared there).
 """
-from . import dense, mps  # noqa: F401
+from . import dense, grad, mps  # noqa: F401
