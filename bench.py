@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle sample")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--shots", type=int, default=1024, help="perfect-sampling shots on the saturated state")
+    ap.add_argument("--grad-reps", type=int, default=3, help="timed energy-gradient evaluations (50-qubit HEA)")
     ap.add_argument("--nonlocal-ops", type=int, default=60,
                     help="gates at distance <= 6 applied to the saturated state by the SWAP method")
     ap.add_argument("--gemm", default="tf32x3", choices=["fp32", "fp32_3m", "tf32x3", "bf16x3"],
@@ -410,6 +411,32 @@ def run_ours(args, world, rank, local):
                                   "one synchronous tnsim_sample call (right environments, uniforms upload "
                                   "and bit read-back included)"}
 
+    # ---- reverse-mode energy gradient (tnsim_grad) of the 50-qubit, 10-layer HEA at chi 64
+    grad_obj = None
+    if args.grad_reps > 0 and rank == 0:
+        nq = 50
+        hcirc, hang = W.hea_circuit(nq, 10, seed=1, sigma=0.3)
+        hl = [(l.pairs, l.g4) for l in hcirc.layers]
+        hax = ["YZ" if i % 2 == 0 else "" for i in range(len(hl))]
+        hth = [hang[i // 2] if i % 2 == 0 else np.zeros((nq, 0)) for i in range(len(hl))]
+        hp = ["".join("Z" if k in (i, i + 1) else "I" for k in range(nq)) for i in range(nq - 1)] + \
+             ["".join("X" if k == i else "I" for k in range(nq)) for i in range(nq)]
+        hc = [1.0] * (nq - 1) + [0.5] * nq
+        gp = T.tnsim_params_default(T.TNSIM_C64)
+        gp.chi_max = 64
+        T.tnsim_grad(nq, hl, hax, hth, hp, hc, T.TNSIM_C64, gp, stream.cuda_stream)   # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.grad_reps):
+            ge, _ = T.tnsim_grad(nq, hl, hax, hth, hp, hc, T.TNSIM_C64, gp, stream.cuda_stream)
+        tg = (time.perf_counter() - t0) / args.grad_reps
+        grad_obj = {"value": 1.0 / tg, "unit": "energy gradients/s (1000 angles each)", "seconds": tg,
+                    "energy": ge,
+                    "sample": "50-qubit hardware-efficient ansatz, 10 layers of RY RZ on every qubit and a CZ "
+                              "ladder, angles N(0, 0.3^2), chi_max 64, complex64, H = sum Z_i Z_i+1 + 0.5 sum X_i; "
+                              "one synchronous tnsim_grad call: forward with checkpoints, final adjoint, "
+                              "recompute and backward of every layer"}
+
     cpu = None
     if rank == 0 and world == 1 and args.cpu_seconds > 0:
         r, gcount, secs = oracle_gate_rate(args.cpu_seconds)
@@ -434,7 +461,7 @@ def run_ours(args, world, rank, local):
                 "config": cfg, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e_obj,
                 "gpu_launches": launches, "clocks": clocks, "plain_path": plain,
                 "vs_plain": (value / plain["value"]) if plain else None, "kernels": kernels,
-                "nonlocal": nonlocal_obj, "sampling": sampling_obj}
+                "nonlocal": nonlocal_obj, "sampling": sampling_obj, "grad": grad_obj}
         print(json.dumps(line), flush=True)
     m.close()
     if dist:

@@ -279,11 +279,47 @@ tnsim_status tnsim_set_jacobi_config(tnsim_mps* m, int32_t cfg);
 tnsim_status tnsim_autotune(tnsim_mps* m, int32_t n2, const int32_t* q, const double* g4x4, int32_t reps,
                             int32_t* choice_out, double* ms_out);
 
-/* Gradient of an energy with respect to gate angles: not in this build
- * (returns EUNSUPPORTED). All pointer arguments are ignored. */
-tnsim_status tnsim_grad(const void* circuit, const double* theta, int32_t n_theta,
-                        const void* hamiltonian, const tnsim_params* p,
-                        double* energy_out, double* grad_out);
+/* A layered circuit for tnsim_grad.  Layer L: every qubit gets n_rot[L] rotations
+ * R_a(t) = exp(-i t P_a / 2) (axes: the n_rot[L] letters 'X','Y','Z' of the layer,
+ * concatenated over layers; the first letter acts first), then n2[L] fixed two-qubit
+ * gates on disjoint pairs (q[...], q[...]+1), 4x4 in g4x4 (32 doubles each), both
+ * concatenated over layers.  The angles theta are laid out layer after layer as
+ * [n_qubits][n_rot[L]]. */
+typedef struct {
+    int32_t n_qubits;
+    int32_t n_layers;
+    const int32_t* n_rot;
+    const char* axes;
+    const int32_t* n2;
+    const int32_t* q;
+    const double* g4x4;
+} tnsim_circuit;
+
+/* H = sum_t coeffs[t] P_t: n_terms Pauli strings of n_qubits letters from 'I','X','Y','Z'. */
+typedef struct {
+    int32_t n_terms;
+    const char* paulis;
+    const double* coeffs;
+} tnsim_hamiltonian;
+
+/* Energy E = <psi|H|psi> / <psi|psi> of the circuit's state from |0...0> and its
+ * gradient with respect to every angle, by reverse-mode differentiation of the
+ * simulation itself (the paper does not differentiate its simulator).  The forward
+ * is the library's layer path (dtype dt, params p: chi_max, cutoff, renormalize;
+ * the paper's form only), with the state checkpointed before every layer.  The
+ * backward starts from the adjoint of the final sites (transfer-matrix environments
+ * of every Pauli term) and, layer by layer in reverse, restores the checkpoint,
+ * recomputes the layer and differentiates each two-qubit update exactly: the new
+ * left site U depends on the gated block T only through the kept subspace, whose
+ * derivative couples kept and discarded singular directions through broadened
+ * 1/(s_j^2 - s_l^2); the renormalisation factor is differentiated too.  So the
+ * gradient is that of the truncated simulation.  cuda_stream: as in
+ * tnsim_mps_create.  energy_out: host double; grad_out: host, sum_L n_qubits *
+ * n_rot[L] doubles.  Synchronous; all device memory is released before return.
+ * Errors: EINVAL (bad circuit, angles or Hamiltonian), EUNSUPPORTED (canonical
+ * form), ENOMEM, ETIMEOUT, ECUDA. */
+tnsim_status tnsim_grad(const tnsim_circuit* c, const double* theta, const tnsim_hamiltonian* h, tnsim_dtype dt,
+                        const tnsim_params* p, void* cuda_stream, double* energy_out, double* grad_out);
 
 /* Work counters accumulated on the device since the previous tnsim_last_stats call
  * on m (then reset).  visit_rows and rotation_rows weight every examined / rotated

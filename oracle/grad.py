@@ -101,7 +101,7 @@ def _env_left(sites, ops):
     envs = [np.ones((1, 1), dtype=np.complex128)]
     for a, o in zip(sites, ops):
         e = envs[-1]
-        envs.append(np.einsum("xy,xpa,pq,yqb->ab", e, a.conj(), o, a))
+        envs.append(np.einsum("xy,xpa,pq,yqb->ab", e, a.conj(), o, a, optimize=True))
     return envs
 
 
@@ -112,7 +112,7 @@ def _env_right(sites, ops):
     envs[n] = np.ones((1, 1), dtype=np.complex128)
     for q in range(n - 1, -1, -1):
         a = sites[q]
-        envs[q] = np.einsum("xpa,pq,yqb,ab->xy", a.conj(), ops[q], a, envs[q + 1])
+        envs[q] = np.einsum("xpa,pq,yqb,ab->xy", a.conj(), ops[q], a, envs[q + 1], optimize=True)
     return envs
 
 
@@ -133,11 +133,11 @@ def final_adjoint(mps: M.MPS, paulis: Sequence[str], coeffs: Sequence[float]):
         Lp, Rp = _env_left(mps.sites, ops), _env_right(mps.sites, ops)
         hsum += c * Lp[n][0, 0].real
         for q in range(n):
-            abar_h[q] += c * np.einsum("xy,pq,yqb,ab->xpa", Lp[q], ops[q], mps.sites[q], Rp[q + 1])
+            abar_h[q] += c * np.einsum("xy,pq,yqb,ab->xpa", Lp[q], ops[q], mps.sites[q], Rp[q + 1], optimize=True)
     e = hsum / nrm
     abar = []
     for q in range(n):
-        an = np.einsum("xy,yqb,ab->xqa", L0[q], mps.sites[q], R0[q + 1])
+        an = np.einsum("xy,yqb,ab->xqa", L0[q], mps.sites[q], R0[q + 1], optimize=True)
         abar.append((abar_h[q] - e * an) / nrm)
     return e, abar
 
@@ -146,7 +146,7 @@ def final_adjoint(mps: M.MPS, paulis: Sequence[str], coeffs: Sequence[float]):
 # backward through the steps
 
 
-def truncation_backward(T, uk, y, s, nz, u_all, ub, yb):
+def truncation_backward(T, uk, y, s, nz, u_all, ub, yb, tau: float = 0.0, broaden: float = 1e-24):
     """Tb for the truncated update T -> (U, Y): U (m x k) the kept left singular vectors
     of T as the forward produced them, Y = U^H T, given Ub and the total Yb.
 
@@ -163,24 +163,35 @@ def truncation_backward(T, uk, y, s, nz, u_all, ub, yb):
     own factors: for degenerate singular values a recomputed SVD may pick another
     basis, and the incoming adjoints refer to the forward's.  s, u_all: a full SVD of
     T (descending; only gauge-invariant parts of it are used); nz: how many s are
-    nonzero.  This is the exact derivative of the truncated map."""
+    nonzero.  This is the exact derivative of the truncated map.
+
+    (I - P) Ut equals (I - P) Ub exactly, since (I - P) T = 0; the latter is used, which
+    avoids dividing the rounding of (I - P) T Yb^H by s_j.  tau > 0: kept directions with
+    s_j <= tau s_max get no inverse factors (a pseudo-inverse cutoff): their rows of
+    S_k^-2 Y and their columns of G are zero.  tau = 0 is the exact derivative.
+    broaden: G_lj = d / (d^2 + broaden s_max^4) with d = s_j^2 - s_l^2 (Lorentzian
+    broadening of the cut's denominators; at a degenerate cut the truncated map is not
+    differentiable and this keeps the result finite)."""
     k = uk.shape[1]
     sk = s[:k]
     ud, sd = u_all[:, k:nz], s[k:nz]
     ut = ub + T @ yb.conj().T
     tb = uk @ yb
     p_all = u_all[:, :nz] @ u_all[:, :nz].conj().T
-    tb += (ut - p_all @ ut) @ (y / (sk * sk)[:, None])
+    live = sk > tau * s[0]
+    inv2 = np.where(live, 1.0 / np.where(live, sk * sk, 1.0), 0.0)
+    tb += (ub - p_all @ ub) @ (y * inv2[:, None])
     if nz > k:
         d = sk[None, :] ** 2 - sd[:, None] ** 2                 # [l, j] = s_j^2 - s_l^2
-        eps_b = 1e-24 * sk[0] ** 4
-        G = d / (d * d + eps_b)
+        eps_b = broaden * sk[0] ** 4
+        G = (d / (d * d + eps_b)) * live[None, :]
         Z = ud @ (G * (ud.conj().T @ ut)) @ uk.conj().T
         tb += (Z + Z.conj().T) @ T
     return tb
 
 
-def gate_backward(a, b, g4, ul, ur, a_new, b_new, ab_new, bb_new, renormalize):
+def gate_backward(a, b, g4, ul, ur, a_new, b_new, ab_new, bb_new, renormalize, tau: float = 0.0,
+                  broaden: float = 1e-24):
     """Backward of one two-qubit update on pre-gate sites a, b (before the one-qubit gates
     ul, ur of the layer, None = identity) that produced a_new (U) and b_new (c Y, c the
     renormalisation factor |T|_F / |Y|_F).  ab_new, bb_new: adjoints of the new sites.
@@ -209,7 +220,7 @@ def gate_backward(a, b, g4, ul, ur, a_new, b_new, ab_new, bb_new, renormalize):
         dldc = 2.0 * float(np.real(np.vdot(Bb, Y)))
         Tb += (dldc * c / (2.0 * F2)) * T
         yb = yb - (dldc * c / (2.0 * K2)) * Y
-    Tb += truncation_backward(T, uk, Y, s, nz, u_all, ub_, yb)
+    Tb += truncation_backward(T, uk, Y, s, nz, u_all, ub_, yb, tau, broaden)
     thb = Tb.reshape(chi_l, 2, 2, chi_r)
     Gt4 = Gt.reshape(2, 2, 2, 2)
     mb = np.einsum("abcd,labr->lcdr", Gt4.conj(), thb)
@@ -223,7 +234,7 @@ def gate_backward(a, b, g4, ul, ur, a_new, b_new, ab_new, bb_new, renormalize):
 
 
 def grad(n: int, layers, axes: List[str], theta: List[np.ndarray], paulis, coeffs, chi_max: int,
-         cutoff: float = 0.0, renormalize: bool = True):
+         cutoff: float = 0.0, renormalize: bool = True, tau: float = 0.0, broaden: float = 1e-24):
     """(E, [dE/dtheta_L]) for the layered circuit; theta[L] has shape [n, len(axes[L])]."""
     final, ckpt = run(n, layers, axes, theta, chi_max, cutoff, renormalize)
     e, abar = final_adjoint(final, paulis, coeffs)
@@ -243,7 +254,8 @@ def grad(n: int, layers, axes: List[str], theta: List[np.ndarray], paulis, coeff
             ur = None if u1 is None else u1[q + 1]
             post = post_states[L]
             ab, bb, ubl, ubr = gate_backward(pre.sites[q], pre.sites[q + 1], g, ul, ur, post.sites[q],
-                                             post.sites[q + 1], abar[q], abar[q + 1], renormalize)
+                                             post.sites[q + 1], abar[q], abar[q + 1], renormalize, tau,
+                                             broaden)
             new_abar[q], new_abar[q + 1] = ab, bb
             ubar[q] += ubl
             ubar[q + 1] += ubr

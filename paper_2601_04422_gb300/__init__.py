@@ -12,7 +12,7 @@ from ._abi import (  # noqa: F401
     tnsim_params, tnsim_params_default, tnsim_mps_create, tnsim_mps_destroy, tnsim_apply_layer,
     tnsim_apply_layer_device, tnsim_apply_layers_batched, tnsim_sync, tnsim_bond_dims,
     tnsim_bond_spectrum, tnsim_export_sites, tnsim_import_sites, tnsim_amplitudes,
-    tnsim_expect_pauli, tnsim_grad, tnsim_last_stats, tnsim_last_error, tnsim_version,
+    tnsim_expect_pauli, tnsim_grad, tnsim_circuit, tnsim_hamiltonian, tnsim_last_stats, tnsim_last_error, tnsim_version,
     tnsim_stats, tnsim_profile_enable, tnsim_profile_read, TNSIM_K_NAMES,
     tnsim_two_site_update_noalloc, tnsim_plan_create, tnsim_plan_launch, tnsim_plan_destroy,
     tnsim_graph_create, tnsim_graph_launch, tnsim_graph_destroy, tnsim_apply_circuit,

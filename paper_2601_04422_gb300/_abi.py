@@ -76,7 +76,17 @@ _sig("tnsim_export_sites", C.c_int, [_P, _DP, C.c_int64, _I64P])
 _sig("tnsim_import_sites", C.c_int, [_P, _I32P, _DP])
 _sig("tnsim_amplitudes", C.c_int, [_P, C.c_int64, C.POINTER(C.c_uint8), _DP])
 _sig("tnsim_expect_pauli", C.c_int, [_P, C.c_int32, C.c_char_p, _DP])
-_sig("tnsim_grad", C.c_int, [_P, _DP, C.c_int32, _P, C.POINTER(tnsim_params), _DP, _DP])
+class tnsim_circuit(C.Structure):
+    _fields_ = [("n_qubits", C.c_int32), ("n_layers", C.c_int32), ("n_rot", _I32P), ("axes", C.c_char_p),
+                ("n2", _I32P), ("q", _I32P), ("g4x4", _DP)]
+
+
+class tnsim_hamiltonian(C.Structure):
+    _fields_ = [("n_terms", C.c_int32), ("paulis", C.c_char_p), ("coeffs", _DP)]
+
+
+_sig("tnsim_grad", C.c_int, [C.POINTER(tnsim_circuit), _DP, C.POINTER(tnsim_hamiltonian), C.c_int,
+                             C.POINTER(tnsim_params), _P, _DP, _DP])
 class tnsim_stats(C.Structure):
     _fields_ = [(k, C.c_int64) for k in ("gates", "sweeps", "rotations", "pair_visits", "visit_rows",
                                           "rotation_rows", "theta_cmacs", "right_cmacs")]
@@ -347,8 +357,37 @@ def tnsim_autotune(h, q, g4x4, reps: int = 3):
     return choice.value, ms
 
 
-def tnsim_grad(*args, **kwargs):
-    _check(lib.tnsim_grad(None, None, 0, None, None, None, None))
+def tnsim_grad(n_qubits: int, layers, axes, theta, paulis, coeffs, dtype: int = TNSIM_C128, params=None,
+               stream=None):
+    """Energy and angle gradient of a layered circuit (reverse mode through the simulation).
+
+    layers[L] = (pairs, g4 [n2, 4, 4]); axes[L] a string of rotation axes (first acts
+    first); theta[L] an array [n_qubits, len(axes[L])]; H = sum coeffs[t] * paulis[t].
+    Returns (E, [dE/dtheta_L])."""
+    n, nl = int(n_qubits), len(layers)
+    n_rot = np.array([len(a) for a in axes] or [0], dtype=np.int32)
+    n2 = np.array([len(np.asarray(pq).reshape(-1)) for pq, _ in layers] or [0], dtype=np.int32)
+    q = np.concatenate([np.asarray(pq, dtype=np.int32).reshape(-1) for pq, _ in layers] + [np.zeros(1, np.int32)])
+    g = np.concatenate([_cplx(g4, (4, 4)).reshape(-1, 4, 4) for _, g4 in layers if len(g4)] +
+                       [np.zeros((1, 4, 4), np.complex128)])
+    th = np.concatenate([np.asarray(t, dtype=np.float64).reshape(-1) for t in theta] + [np.zeros(1)])
+    ax = "".join(axes).encode()
+    c = tnsim_circuit(n, nl, n_rot.ctypes.data_as(_I32P), ax, n2.ctypes.data_as(_I32P), q.ctypes.data_as(_I32P),
+                      _dptr(g.view(np.float64)))
+    ps = "".join(paulis).encode()
+    co = np.ascontiguousarray(coeffs, dtype=np.float64)
+    h = tnsim_hamiltonian(len(paulis), ps, _dptr(co))
+    e = C.c_double(0.0)
+    grad = np.zeros(max(int(sum(n * len(a) for a in axes)), 1))
+    _check(lib.tnsim_grad(C.byref(c), _dptr(th), C.byref(h), int(dtype),
+                          C.byref(params) if params is not None else None, _P(int(stream)) if stream else None,
+                          C.byref(e), _dptr(grad)))
+    out, off = [], 0
+    for a in axes:
+        k = n * len(a)
+        out.append(grad[off:off + k].reshape(n, len(a)).copy())
+        off += k
+    return e.value, out
 
 
 def tnsim_last_stats(h) -> dict:

@@ -165,6 +165,17 @@ cudaError_t launch_transfer(const void* site, const int* chi, int q, const doubl
     return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_apply_rt(const void* site, const int* chi, int q, const void* rt, void* tmp, int chi_cap,
+                            cudaStream_t s) {
+    using C = typename CT<T>::type;
+    const int64_t n1 = (int64_t)chi_cap * 2 * chi_cap;
+    k_tr1<T><<<(unsigned)((n1 + 255) / 256), 256, 0, s>>>((const C*)site, chi, q, (const C*)rt, (C*)tmp);
+    return cudaGetLastError();
+}
+template cudaError_t launch_apply_rt<float>(const void*, const int*, int, const void*, void*, int, cudaStream_t);
+template cudaError_t launch_apply_rt<double>(const void*, const int*, int, const void*, void*, int, cudaStream_t);
+
 // <L | R>-style closure: out = sum_{x,y} E[x,y] Rt[y,x] over one bond, E and Rt both chi x chi
 template <typename T>
 __global__ void k_close(const typename CT<T>::type* __restrict__ E, const typename CT<T>::type* __restrict__ Rt,

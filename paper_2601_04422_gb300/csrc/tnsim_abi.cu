@@ -68,6 +68,7 @@ struct tnsim_mps {
     size_t esz = 8;
     std::vector<int> cap, ub;
     std::vector<size_t> site_off;  // byte offsets into d_sites
+    size_t arena_bytes = 0;        // size of d_sites
     int G = 0, capmax = 1;
     size_t ws_elems = 0;
     char* d_sites = nullptr;
@@ -509,6 +510,7 @@ tnsim_status tnsim_mps_create(int32_t n_qubits, tnsim_dtype dt, const tnsim_para
         }                                                                        \
     } while (0)
 
+    m->arena_bytes = off;
     ALLOC(m->d_sites, off);
     ALLOC(m->d_chi, sizeof(int) * (n_qubits + 1));
     ALLOC(m->d_ws, nG * 2 * m->ws_elems * m->esz);
@@ -1425,9 +1427,339 @@ tnsim_status tnsim_autotune(tnsim_mps* m, int32_t n2, const int32_t* q, const do
     return TNSIM_OK;
 }
 
-tnsim_status tnsim_grad(const void*, const double*, int32_t, const void*, const tnsim_params*,
-                        double*, double*) {
-    return fail(TNSIM_EUNSUPPORTED, "tnsim_grad is not built yet");
+tnsim_status tnsim_grad(const tnsim_circuit* c, const double* theta, const tnsim_hamiltonian* h, tnsim_dtype dt,
+                        const tnsim_params* p, void* cuda_stream, double* energy_out, double* grad_out) {
+    // ---- validation (nothing is allocated before it passes)
+    if (!c || !theta || !h || !energy_out) return fail(TNSIM_EINVAL, "NULL argument");
+    const int n = c->n_qubits, nl = c->n_layers;
+    if (n < 2 || nl < 0) return fail(TNSIM_EINVAL, "bad circuit size");
+    if (nl > 0 && (!c->n_rot || !c->n2)) return fail(TNSIM_EINVAL, "NULL layer arrays");
+    if (dt != TNSIM_C64 && dt != TNSIM_C128) return fail(TNSIM_EINVAL, "unknown dtype");
+    tnsim_params prm;
+    tnsim_params_default(dt, &prm);
+    if (p) prm = *p;
+    tnsim_status s = check_params(&prm);
+    if (s != TNSIM_OK) return s;
+    if (prm.form != TNSIM_FORM_PAPER) return fail(TNSIM_EUNSUPPORTED, "tnsim_grad differentiates the paper's form only");
+    std::vector<int64_t> rot_off(nl + 1, 0), gate_off(nl + 1, 0), ax_off(nl + 1, 0);
+    for (int L = 0; L < nl; ++L) {
+        if (c->n_rot[L] < 0 || c->n_rot[L] > 8) return fail(TNSIM_EINVAL, "n_rot must be in [0, 8]");
+        if (c->n2[L] < 0 || c->n2[L] > n / 2) return fail(TNSIM_EINVAL, "bad pair count");
+        ax_off[L + 1] = ax_off[L] + c->n_rot[L];
+        rot_off[L + 1] = rot_off[L] + (int64_t)c->n_rot[L] * n;
+        gate_off[L + 1] = gate_off[L] + c->n2[L];
+    }
+    if (ax_off[nl] > 0 && !c->axes) return fail(TNSIM_EINVAL, "NULL axes");
+    for (int64_t i = 0; i < ax_off[nl]; ++i)
+        if (c->axes[i] != 'X' && c->axes[i] != 'Y' && c->axes[i] != 'Z') return fail(TNSIM_EINVAL, "axes must be X, Y or Z");
+    if (gate_off[nl] > 0 && (!c->q || !c->g4x4)) return fail(TNSIM_EINVAL, "NULL gate arrays");
+    if (rot_off[nl] > 0 && !grad_out) return fail(TNSIM_EINVAL, "grad_out is NULL");
+    for (int L = 0; L < nl; ++L) {
+        std::vector<char> used(n, 0);
+        for (int64_t i = gate_off[L]; i < gate_off[L + 1]; ++i) {
+            const int q = c->q[i];
+            if (q < 0 || q >= n - 1 || used[q] || used[q + 1]) return fail(TNSIM_EINVAL, "bad or overlapping pair");
+            used[q] = used[q + 1] = 1;
+        }
+    }
+    if (!finite_all(c->g4x4, (size_t)gate_off[nl] * 32) || !finite_all(theta, (size_t)rot_off[nl]))
+        return fail(TNSIM_EINVAL, "non-finite gate entry or angle");
+    if (h->n_terms < 1 || !h->paulis || !h->coeffs) return fail(TNSIM_EINVAL, "empty Hamiltonian");
+    struct Term { int a, b; double coef; int idx; };
+    std::vector<Term> terms;
+    double id_coef = 0.0;
+    for (int t = 0; t < h->n_terms; ++t) {
+        int a = -1, b = -1;
+        for (int q = 0; q < n; ++q) {
+            const char ch = h->paulis[(size_t)t * n + q];
+            if (ch != 'I' && ch != 'X' && ch != 'Y' && ch != 'Z') return fail(TNSIM_EINVAL, "Pauli characters must be I, X, Y, Z");
+            if (ch != 'I') { if (a < 0) a = q; b = q; }
+        }
+        if (!std::isfinite(h->coeffs[t])) return fail(TNSIM_EINVAL, "non-finite coefficient");
+        if (a < 0) id_coef += h->coeffs[t];
+        else terms.push_back({a, b, h->coeffs[t], t});
+    }
+    // ---- a state of our own on the caller's stream
+    tnsim_mps* m = nullptr;
+    s = tnsim_mps_create(n, dt, &prm, cuda_stream, &m);
+    if (s != TNSIM_OK) return s;
+    struct Guard { tnsim_mps* m; std::vector<void*> bufs;
+        ~Guard() { if (m) cudaStreamSynchronize(m->stream); for (void* b : bufs) cudaFree(b); if (m) tnsim_mps_destroy(m); } } gd{m, {}};
+    DevGuard dg(m->device);
+    cudaStream_t st = m->stream;
+    const size_t es = m->esz, AB = m->arena_bytes;
+    int cap_max = 1;
+    for (int b = 0; b <= n; ++b) cap_max = std::max(cap_max, m->cap[b]);
+    const size_t env = (size_t)cap_max * cap_max * es;
+    const size_t cm = 2 * (size_t)m->capmax;
+    auto dalloc = [&](size_t bytes) -> char* {
+        void* ptr = nullptr;
+        if (cudaMalloc(&ptr, std::max<size_t>(bytes, 256)) != cudaSuccess) return nullptr;
+        gd.bufs.push_back(ptr);
+        return (char*)ptr;
+    };
+    const int64_t n_theta = rot_off[nl];
+    const int64_t n_gates_all = gate_off[nl];
+    char* d_theta = dalloc(sizeof(double) * std::max<int64_t>(n_theta, 1));
+    char* d_axes = dalloc(std::max<int64_t>(ax_off[nl], 1));
+    double* d_u1 = (double*)dalloc(sizeof(double) * 8 * (size_t)std::max<int64_t>(n_theta, 1) * 1);
+    double* d_ubar = (double*)dalloc(sizeof(double) * 8 * (size_t)std::max<int64_t>(n_theta, 1) + sizeof(double) * 16 * m->G);
+    double* d_grad = (double*)dalloc(sizeof(double) * std::max<int64_t>(n_theta, 1));
+    double* d_g4 = (double*)dalloc(sizeof(double) * 32 * std::max<int64_t>(n_gates_all, 1));
+    RotLayer* d_rl = (RotLayer*)dalloc(sizeof(RotLayer) * std::max(nl, 1));
+    char* d_ckpt = dalloc((AB + sizeof(int) * (n + 1) + 255) / 256 * 256 * (size_t)(nl + 1));
+    char* d_env = dalloc(env * (size_t)(4 * (n + 1) + 4) + env * 2 * terms.size());
+    char* d_adj = dalloc(AB * 4);
+    char* d_scr = dalloc(9 * cm * cm * es * (size_t)m->G);
+    GradGateDesc* d_gdesc = (GradGateDesc*)dalloc(sizeof(GradGateDesc) * m->G);
+    Site1Bwd* d_s1 = (Site1Bwd*)dalloc(sizeof(Site1Bwd) * n);
+    double* d_ops = (double*)dalloc(sizeof(double) * 32);
+    if (!d_theta || !d_axes || !d_u1 || !d_ubar || !d_grad || !d_g4 || !d_rl || !d_ckpt || !d_env || !d_adj || !d_scr ||
+        !d_gdesc || !d_s1 || !d_ops)
+        return fail(TNSIM_ENOMEM, "tnsim_grad: device allocation failed");
+    // one 2x2 gate per (layer with rotations, qubit)
+    std::vector<int64_t> u1_off(nl, -1);
+    int64_t u1n = 0;
+    for (int L = 0; L < nl; ++L)
+        if (c->n_rot[L] > 0) { u1_off[L] = u1n; u1n += (int64_t)n * 8; }
+    std::vector<RotLayer> rl(std::max(nl, 1));
+    for (int L = 0; L < nl; ++L) {
+        rl[L].axes = d_axes + ax_off[L];
+        rl[L].theta = (const double*)d_theta + rot_off[L];
+        rl[L].n_rot = c->n_rot[L];
+        rl[L].pad_ = 0;
+        rl[L].u1_off = std::max<int64_t>(u1_off[L], 0);
+        rl[L].grad_off = rot_off[L];
+    }
+    const double ops[4][8] = {{1, 0, 0, 0, 0, 0, 1, 0}, {0, 0, 1, 0, 1, 0, 0, 0},
+                              {0, 0, 0, -1, 0, 1, 0, 0}, {1, 0, 0, 0, 0, 0, -1, 0}};
+    auto opi = [](char ch) { return ch == 'I' ? 0 : ch == 'X' ? 1 : ch == 'Y' ? 2 : 3; };
+    CUDA_TRY(cudaMemcpyAsync(d_ops, ops, sizeof(ops), cudaMemcpyHostToDevice, st));
+    if (n_theta > 0) CUDA_TRY(cudaMemcpyAsync(d_theta, theta, sizeof(double) * n_theta, cudaMemcpyHostToDevice, st));
+    if (ax_off[nl] > 0) CUDA_TRY(cudaMemcpyAsync(d_axes, c->axes, ax_off[nl], cudaMemcpyHostToDevice, st));
+    if (n_gates_all > 0) CUDA_TRY(cudaMemcpyAsync(d_g4, c->g4x4, sizeof(double) * 32 * n_gates_all, cudaMemcpyHostToDevice, st));
+    if (nl > 0) CUDA_TRY(cudaMemcpyAsync(d_rl, rl.data(), sizeof(RotLayer) * nl, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemsetAsync(d_ubar, 0, sizeof(double) * 8 * (size_t)std::max<int64_t>(n_theta, 1) + sizeof(double) * 16 * m->G, st));
+    if (nl > 0) CUDA_TRY(launch_rot_build(d_rl, nl, n, d_u1, st));
+    // every checkpoint starts on a 256-byte boundary (its sites are read with 16-byte accesses)
+    const size_t ck_stride = (AB + sizeof(int) * (n + 1) + 255) / 256 * 256;
+    auto ck_sites = [&](int L) { return d_ckpt + ck_stride * (size_t)L; };
+    auto ck_chi = [&](int L) { return (int*)(d_ckpt + ck_stride * (size_t)L + AB); };
+    auto layer_u1 = [&](int L) -> const double* { return c->n_rot[L] > 0 ? d_u1 + u1_off[L] : nullptr; };
+    auto run_layer = [&](int L) -> tnsim_status {
+        Staging* stg = acquire_staging(m);
+        tnsim_status r = enqueue_layer(m, stg, c->n2[L], c->q + gate_off[L], d_g4 + gate_off[L] * 32, layer_u1(L), nullptr);
+        cudaEventRecord(stg->done, st);
+        return r;
+    };
+    // ---- forward with a checkpoint before every layer (and of the final state)
+    for (int L = 0; L <= nl; ++L) {
+        CUDA_TRY(cudaMemcpyAsync(ck_sites(L), m->d_sites, AB, cudaMemcpyDeviceToDevice, st));
+        CUDA_TRY(cudaMemcpyAsync(ck_chi(L), m->d_chi, sizeof(int) * (n + 1), cudaMemcpyDeviceToDevice, st));
+        if (L < nl) {
+            s = run_layer(L);
+            if (s != TNSIM_OK) return s;
+        }
+    }
+    std::vector<int> chi_h((size_t)(nl + 1) * (n + 1));
+    for (int L = 0; L <= nl; ++L)
+        CUDA_TRY(cudaMemcpyAsync(chi_h.data() + (size_t)L * (n + 1), ck_chi(L), sizeof(int) * (n + 1),
+                                 cudaMemcpyDeviceToHost, st));
+    int sticky = 0;
+    CUDA_TRY(cudaMemcpyAsync(&sticky, m->d_sticky, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (sticky == 5) return fail(TNSIM_ETIMEOUT, "the Jacobi kernel saw no progress (forward incomplete)");
+    auto chi_at = [&](int L, int b) { return chi_h[(size_t)L * (n + 1) + b]; };
+    // ---- energy and the adjoint of the final state (environments of the final state)
+    const int* dchi = m->d_chi;   // the final bond dimensions
+    char* L0 = d_env;
+    char* R0 = L0 + env * (n + 1);
+    char* LH = R0 + env * (n + 1);
+    char* RH = LH + env * (n + 1);
+    char* tmp = RH + env * (n + 1);            // 2 env
+    char* part = tmp + env * 2;                // 2 env (running partial)
+    char* full = part + env * 2;               // 2 env per term (left full, right full)
+    char* AH = d_adj;                          // adjoint of <H> (arena layout)
+    char* AN = d_adj + AB;                     // adjoint of the norm
+    char* ABc = d_adj + 2 * AB;                // adjoint of the current (post-layer) state
+    char* ABn = d_adj + 3 * AB;
+    std::vector<char> one(es, 0);
+    if (dt == TNSIM_C64) { const float f = 1.0f; std::memcpy(one.data(), &f, 4); }
+    else { const double f = 1.0; std::memcpy(one.data(), &f, 8); }
+    CUDA_TRY(cudaMemsetAsync(d_env, 0, env * (size_t)(4 * (n + 1) + 4) + env * 2 * terms.size(), st));
+    CUDA_TRY(cudaMemsetAsync(d_adj, 0, AB * 4, st));
+    CUDA_TRY(cudaMemcpyAsync(L0, one.data(), es, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(R0 + env * n, one.data(), es, cudaMemcpyHostToDevice, st));
+    const bool c64 = dt == TNSIM_C64;
+    auto transfer = [&](int q, const double* op, const char* ein, char* eout, int left) -> cudaError_t {
+        return c64 ? launch_transfer<float>(site_ptr(m, q), dchi, q, op, ein, tmp, eout, cap_max, left, st)
+                   : launch_transfer<double>(site_ptr(m, q), dchi, q, op, ein, tmp, eout, cap_max, left, st);
+    };
+    auto site_adj = [&](int q, const char* E, const double* op, const char* Rt, double coef, char* out) -> cudaError_t {
+        cudaError_t e = c64 ? launch_apply_rt<float>(site_ptr(m, q), dchi, q, Rt, tmp, cap_max, st)
+                            : launch_apply_rt<double>(site_ptr(m, q), dchi, q, Rt, tmp, cap_max, st);
+        if (e != cudaSuccess) return e;
+        return c64 ? launch_site_adj2<float>(E, op, tmp, dchi, q, coef, out + m->site_off[q], cap_max, st)
+                   : launch_site_adj2<double>(E, op, tmp, dchi, q, coef, out + m->site_off[q], cap_max, st);
+    };
+    auto axpy = [&](char* dst, const char* src, int bond, double coef, int zero_first) -> cudaError_t {
+        return c64 ? launch_env_axpy<float>(dst, src, dchi, bond, coef, zero_first, cap_max, st)
+                   : launch_env_axpy<double>(dst, src, dchi, bond, coef, zero_first, cap_max, st);
+    };
+    const double* opI = d_ops;
+    for (int q = 0; q < n; ++q) CUDA_TRY(transfer(q, opI, L0 + env * q, L0 + env * (q + 1), 1));
+    for (int q = n - 1; q >= 0; --q) CUDA_TRY(transfer(q, opI, R0 + env * (q + 1), R0 + env * q, 0));
+    // every non-identity term: the sites it covers, and its full left / right environments
+    for (size_t t = 0; t < terms.size(); ++t) {
+        const Term& tm = terms[t];
+        const char* ps = h->paulis + (size_t)tm.idx * n;
+        char* Lfull = full + env * 2 * t;
+        char* Rfull = Lfull + env;
+        // every site of the support: left partial over a..q-1, right partial over q+1..b
+        // (recomputed per site; Pauli supports are short)
+        for (int q = tm.a; q <= tm.b; ++q) {
+            // left partial over a..q-1 into part[0]
+            CUDA_TRY(cudaMemcpyAsync(part, L0 + env * tm.a, env, cudaMemcpyDeviceToDevice, st));
+            for (int x = tm.a; x < q; ++x) {
+                CUDA_TRY(transfer(x, d_ops + 8 * opi(ps[x]), part, part + env, 1));
+                CUDA_TRY(cudaMemcpyAsync(part, part + env, env, cudaMemcpyDeviceToDevice, st));
+            }
+            // right partial over q+1..b into Rfull (scratch)
+            CUDA_TRY(cudaMemcpyAsync(Rfull, R0 + env * (tm.b + 1), env, cudaMemcpyDeviceToDevice, st));
+            for (int x = tm.b; x > q; --x) {
+                CUDA_TRY(transfer(x, d_ops + 8 * opi(ps[x]), Rfull, part + env, 0));
+                CUDA_TRY(cudaMemcpyAsync(Rfull, part + env, env, cudaMemcpyDeviceToDevice, st));
+            }
+            CUDA_TRY(site_adj(q, part, d_ops + 8 * opi(ps[q]), Rfull, tm.coef, AH));
+        }
+        // full environments of the term
+        CUDA_TRY(cudaMemcpyAsync(Lfull, L0 + env * tm.a, env, cudaMemcpyDeviceToDevice, st));
+        for (int x = tm.a; x <= tm.b; ++x) {
+            CUDA_TRY(transfer(x, d_ops + 8 * opi(ps[x]), Lfull, part, 1));
+            CUDA_TRY(cudaMemcpyAsync(Lfull, part, env, cudaMemcpyDeviceToDevice, st));
+        }
+        CUDA_TRY(cudaMemcpyAsync(Rfull, R0 + env * (tm.b + 1), env, cudaMemcpyDeviceToDevice, st));
+        for (int x = tm.b; x >= tm.a; --x) {
+            CUDA_TRY(transfer(x, d_ops + 8 * opi(ps[x]), Rfull, part, 0));
+            CUDA_TRY(cudaMemcpyAsync(Rfull, part, env, cudaMemcpyDeviceToDevice, st));
+        }
+    }
+    // LH[q]: terms entirely left of bond q; RH[q]: terms entirely right of it
+    CUDA_TRY(axpy(LH, L0, 0, id_coef, 1));
+    for (int q = 0; q < n; ++q) {
+        CUDA_TRY(transfer(q, opI, LH + env * q, LH + env * (q + 1), 1));
+        for (size_t t = 0; t < terms.size(); ++t)
+            if (terms[t].b == q) CUDA_TRY(axpy(LH + env * (q + 1), full + env * 2 * t, q + 1, terms[t].coef, 0));
+    }
+    for (int q = n - 1; q >= 0; --q) {
+        CUDA_TRY(transfer(q, opI, RH + env * (q + 1), RH + env * q, 0));
+        for (size_t t = 0; t < terms.size(); ++t)
+            if (terms[t].a == q) CUDA_TRY(axpy(RH + env * q, full + env * 2 * t + env, q, terms[t].coef, 0));
+    }
+    for (int q = 0; q < n; ++q) {
+        CUDA_TRY(site_adj(q, LH + env * q, opI, R0 + env * (q + 1), 1.0, AH));
+        CUDA_TRY(site_adj(q, L0 + env * q, opI, RH + env * (q + 1), 1.0, AH));
+        CUDA_TRY(site_adj(q, L0 + env * q, opI, R0 + env * (q + 1), 1.0, AN));
+    }
+    // energy = LH[n] / L0[n]
+    double hs[2] = {0, 0}, nr[2] = {0, 0};
+    if (c64) {
+        float a2[2], b2[2];
+        CUDA_TRY(cudaMemcpyAsync(a2, LH + env * n, 8, cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaMemcpyAsync(b2, L0 + env * n, 8, cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        hs[0] = a2[0]; nr[0] = b2[0];
+    } else {
+        CUDA_TRY(cudaMemcpyAsync(hs, LH + env * n, 16, cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaMemcpyAsync(nr, L0 + env * n, 16, cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    *energy_out = hs[0] / nr[0];
+    const int64_t arena_elems = (int64_t)(AB / es);
+    CUDA_TRY(c64 ? launch_adj_combine<float>(AH, AN, LH + env * n, L0 + env * n, arena_elems, st)
+                 : launch_adj_combine<double>(AH, AN, LH + env * n, L0 + env * n, arena_elems, st));
+    CUDA_TRY(cudaMemcpyAsync(ABc, AH, AB, cudaMemcpyDeviceToDevice, st));
+    // ---- backward, layer by layer: restore, recompute, differentiate every gate
+    std::vector<GradGateDesc> hg(m->G);
+    std::vector<Site1Bwd> hs1(n);
+    for (int L = nl - 1; L >= 0; --L) {
+        CUDA_TRY(cudaMemcpyAsync(m->d_sites, ck_sites(L), AB, cudaMemcpyDeviceToDevice, st));
+        CUDA_TRY(cudaMemcpyAsync(m->d_chi, ck_chi(L), sizeof(int) * (n + 1), cudaMemcpyDeviceToDevice, st));
+        for (int b = 0; b <= n; ++b) m->ub[b] = chi_at(L, b);
+        s = run_layer(L);
+        if (s != TNSIM_OK) return s;
+        CUDA_TRY(cudaMemsetAsync(ABn, 0, AB, st));
+        const int n2 = c->n2[L];
+        const int32_t* ql = c->q + gate_off[L];
+        const double* u1 = layer_u1(L);
+        std::vector<char> paired(n, 0);
+        for (int i = 0; i < n2; ++i) {
+            const int q = ql[i];
+            paired[q] = paired[q + 1] = 1;
+            GradGateDesc& d = hg[i];
+            std::memset(&d, 0, sizeof(d));
+            char* ws = m->d_ws + (size_t)i * 2 * m->ws_elems * es;
+            d.a_pre = ck_sites(L) + m->site_off[q];
+            d.b_pre = ck_sites(L) + m->site_off[q + 1];
+            d.u_post = ck_sites(L + 1) + m->site_off[q];
+            d.y_post = ck_sites(L + 1) + m->site_off[q + 1];
+            d.theta0 = ws;
+            d.W = ws + m->ws_elems * es;
+            d.s2 = m->d_s2 + (size_t)i * 2 * m->capmax;
+            d.perm = m->d_perm + (size_t)i * 2 * m->capmax;
+            d.g4 = d_g4 + (gate_off[L] + i) * 32;
+            d.uL = u1 ? u1 + (size_t)q * 8 : nullptr;
+            d.uR = u1 ? u1 + (size_t)(q + 1) * 8 : nullptr;
+            d.ub_post = ABc + m->site_off[q];
+            d.bb_post = ABc + m->site_off[q + 1];
+            d.ab_pre = ABn + m->site_off[q];
+            d.bb_pre = ABn + m->site_off[q + 1];
+            double* ub0 = u1 ? d_ubar + u1_off[L] : d_ubar + (size_t)8 * std::max<int64_t>(n_theta, 1);
+            d.ubar_l = u1 ? ub0 + (size_t)q * 8 : ub0 + (size_t)i * 16;
+            d.ubar_r = u1 ? ub0 + (size_t)(q + 1) * 8 : ub0 + (size_t)i * 16 + 8;
+            d.scratch = d_scr + (size_t)i * 9 * cm * cm * es;
+            d.chiL = chi_at(L, q);
+            d.chiM = chi_at(L, q + 1);
+            d.chiR = chi_at(L, q + 2);
+            d.k = chi_at(L + 1, q + 1);
+            d.renorm = prm.renormalize ? 1 : 0;
+            d.cm = (int)cm;
+        }
+        if (n2 > 0) {
+            CUDA_TRY(cudaMemcpyAsync(d_gdesc, hg.data(), sizeof(GradGateDesc) * n2, cudaMemcpyHostToDevice, st));
+            CUDA_TRY(c64 ? launch_gate_bwd<float>(d_gdesc, n2, st) : launch_gate_bwd<double>(d_gdesc, n2, st));
+        }
+        int ns = 0;
+        for (int q = 0; q < n; ++q) {
+            if (paired[q]) continue;
+            const size_t bytes = (size_t)chi_at(L, q) * 2 * chi_at(L, q + 1) * es;
+            if (!u1) {
+                CUDA_TRY(cudaMemcpyAsync(ABn + m->site_off[q], ABc + m->site_off[q], bytes, cudaMemcpyDeviceToDevice, st));
+                continue;
+            }
+            Site1Bwd& d = hs1[ns++];
+            d.ab_post = ABc + m->site_off[q];
+            d.a_pre = ck_sites(L) + m->site_off[q];
+            d.ab_pre = ABn + m->site_off[q];
+            d.u = u1 + (size_t)q * 8;
+            d.ubar = d_ubar + u1_off[L] + (size_t)q * 8;
+            d.cl = chi_at(L, q);
+            d.cr = chi_at(L, q + 1);
+        }
+        if (ns > 0) {
+            CUDA_TRY(cudaMemcpyAsync(d_s1, hs1.data(), sizeof(Site1Bwd) * ns, cudaMemcpyHostToDevice, st));
+            CUDA_TRY(c64 ? launch_site1_bwd<float>(d_s1, ns, st) : launch_site1_bwd<double>(d_s1, ns, st));
+        }
+        // the host arrays above are read by the copies before the next layer reuses them
+        CUDA_TRY(cudaStreamSynchronize(st));
+        std::swap(ABc, ABn);
+    }
+    if (n_theta > 0) {
+        CUDA_TRY(launch_rot_grad(d_rl, nl, n, d_ubar, d_grad, st));
+        CUDA_TRY(cudaMemcpyAsync(grad_out, d_grad, sizeof(double) * n_theta, cudaMemcpyDeviceToHost, st));
+    }
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return TNSIM_OK;
 }
 
 tnsim_status tnsim_last_stats(tnsim_mps* m, tnsim_stats* out) {

@@ -151,6 +151,71 @@ cudaError_t launch_sample_site(const void* site, int cl, int cr, const void* rt_
                                int64_t shots, int node_bound, const double* u, uint8_t* bits,
                                SampleWork& w, cudaStream_t s);
 
+// ---------------------------------------------------------------------------
+// Reverse-mode gradient (k_grad.cu)
+
+// One two-qubit update to differentiate (device memory, one per gate of a layer).
+struct GradGateDesc {
+    const void* a_pre;    // pre-layer site q   (chiL, 2, chiM)
+    const void* b_pre;    // pre-layer site q+1 (chiM, 2, chiR)
+    const void* u_post;   // post-layer site q  (chiL, 2, k)  = U
+    const void* y_post;   // post-layer site q+1 (k, 2, chiR) = c Y
+    const void* theta0;   // the gated block T, column-major (2chiL) x (2chiR)
+    const void* W;        // the Jacobi columns of the same layer, column-major
+    const double* s2;     // sorted squared column norms of W (2chiR)
+    const int* perm;      // their columns
+    const double* g4;     // the 4x4 gate
+    const double* uL;     // the layer's one-qubit gates of q, q+1 (or null)
+    const double* uR;
+    const void* ub_post;  // adjoint of the post-layer site q
+    const void* bb_post;  // adjoint of the post-layer site q+1
+    void* ab_pre;         // adjoint of the pre-layer site q (written)
+    void* bb_pre;         // adjoint of the pre-layer site q+1 (written)
+    double* ubar_l;       // 2x2 adjoints of uL, uR (accumulated)
+    double* ubar_r;
+    void* scratch;        // 9 cm^2 complex elements
+    int chiL, chiM, chiR, k;
+    int renorm;
+    int cm;               // 2 chi_cap: bound of m = 2 chiL, n = 2 chiR and k
+};
+// An unpaired site of a layer with a one-qubit gate.
+struct Site1Bwd {
+    const void* ab_post;  // adjoint of the post-layer site (cl, 2, cr)
+    const void* a_pre;    // the pre-layer site
+    void* ab_pre;         // adjoint of the pre-layer site (written)
+    const double* u;      // the gate
+    double* ubar;         // its 2x2 adjoint (accumulated)
+    int cl, cr;
+};
+// The rotations of one layer (device pointers).
+struct RotLayer {
+    const char* axes;     // n_rot axis letters, the first acts first
+    const double* theta;  // [n_qubits][n_rot]
+    int n_rot;
+    int pad_;
+    int64_t u1_off;       // offset (doubles) of this layer's one-qubit gates in the u1 buffer
+    int64_t grad_off;     // offset of its angles in the gradient
+};
+template <typename T>
+cudaError_t launch_gate_bwd(const GradGateDesc* d, int n_gates, cudaStream_t s);
+template <typename T>
+cudaError_t launch_site1_bwd(const Site1Bwd* d, int n_sites, cudaStream_t s);
+template <typename T>
+cudaError_t launch_env_axpy(void* dst, const void* src, const int* chi, int bond, double coef, int zero_first,
+                            int chi_cap, cudaStream_t s);
+template <typename T>
+cudaError_t launch_site_adj2(const void* E, const double* op, const void* tmp, const int* chi, int q, double coef,
+                             void* out, int chi_cap, cudaStream_t s);
+template <typename T>
+cudaError_t launch_adj_combine(void* ah, const void* an, const void* hsum, const void* nrm, int64_t count,
+                               cudaStream_t s);
+cudaError_t launch_rot_build(const RotLayer* rl, int n_layers, int n, double* u1, cudaStream_t s);
+cudaError_t launch_rot_grad(const RotLayer* rl, int n_layers, int n, const double* ub, double* grad, cudaStream_t s);
+// tmp[y, p, a] = sum_b A_q[y, p, b] Rt[b, a]: a site times a (transposed) right environment
+template <typename T>
+cudaError_t launch_apply_rt(const void* site, const int* chi, int q, const void* rt, void* tmp, int chi_cap,
+                            cudaStream_t s);
+
 // Set the thread-local message returned by tnsim_last_error().
 void set_last_error(const char* msg);
 
