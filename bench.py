@@ -339,7 +339,9 @@ def run_ours(args, world, rank, local):
     # ---- roofline of the dominant kernel (the Jacobi SVD), FP32 ALU bound
     pk = peaks()
     jac_ms, jac_n = prof["jacobi"]
-    flops = 16.0 * stats["visit_rows"] + 20.0 * stats["rotation_rows"]
+    # per examined pair-row: g = x_i^H x_j (4 FMA); per rotated pair-row: both columns updated (20 flops);
+    # the column norms are tracked, not recomputed per pair
+    flops = 8.0 * stats["visit_rows"] + 20.0 * stats["rotation_rows"]
     achieved = flops / (jac_ms / 1000.0) / 1e12 if jac_ms > 0 else 0.0
     sm_mhz = pk["sm_max_mhz"]
     peak = fp32_alu_peak_tflops(sm_mhz)

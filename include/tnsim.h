@@ -324,7 +324,8 @@ tnsim_status tnsim_grad(const tnsim_circuit* c, const double* theta, const tnsim
 /* Work counters accumulated on the device since the previous tnsim_last_stats call
  * on m (then reset).  visit_rows and rotation_rows weight every examined / rotated
  * column pair by its column length m = 2 chi_L, so the Jacobi SVD's arithmetic is
- * 16 visit_rows + 20 rotation_rows real flops (FMA = 2). */
+ * 8 visit_rows + 20 rotation_rows real flops (FMA = 2): an examined pair forms
+ * g = x_i^H x_j, the column norms being tracked, and a rotation updates both columns. */
 typedef struct {
     int64_t gates;         /* two-qubit gates applied */
     int64_t sweeps;        /* Jacobi sweeps, summed over gates */

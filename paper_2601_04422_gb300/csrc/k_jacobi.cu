@@ -18,7 +18,8 @@
 // blocks once in round-robin ("circle") order: P - 1 rounds of P/2 disjoint block
 // pairs.  A visit stages both blocks in shared memory, rotates the BC x BC cross
 // pairs in BC rounds of BC disjoint pairs (one warp per pair, lanes over rows,
-// warp-shuffle reductions; each warp keeps its block-I column in registers) and, in
+// warp-shuffle reductions; each warp keeps its block-I column in registers, and the
+// column norms are tracked rather than recomputed per pair) and, in
 // the first round of a sweep, the pairs inside each block as well, then writes the
 // blocks back.  Each sweep therefore rotates every column pair exactly once.  A sweep
 // that rotates nothing ends the gate's iteration; reaching max_sweeps sets ENOCONV.
@@ -107,10 +108,11 @@ __device__ __forceinline__ int rotate_pair(C* __restrict__ xi, C* __restrict__ x
 // c - 1 = -t^2 / (rr (1 + rr)) is formed without cancellation.  FP64 keeps IEEE
 // operations throughout.
 __device__ __forceinline__ bool rot_params_fast(float a, float b, float gr, float gi, float tol2, float zthr,
-                                                float& cm1, float& sr, float& si) {
+                                                float& cm1, float& sr, float& si, float& tg) {
     const float g2 = gr * gr + gi * gi;
     if (!(a > zthr && b > zthr && __fdividef(g2, b) > tol2 * a)) return false;
-    const float rg = __frcp_rn(sqrtf(g2));                // 1 / |g|
+    const float gabs = sqrtf(g2);
+    const float rg = __frcp_rn(gabs);                     // 1 / |g|
     const float zeta = 0.5f * (b - a) * rg;
     const float az = fabsf(zeta);
     // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)); for |zeta| > 2^12, 1 + zeta^2 rounds to zeta^2
@@ -122,10 +124,11 @@ __device__ __forceinline__ bool rot_params_fast(float a, float b, float gr, floa
     const float sv = t * irr;
     sr = sv * (gr * rg);
     si = sv * (gi * rg);
+    tg = t * gabs;                                        // the norms become a - t|g|, b + t|g|
     return true;
 }
 __device__ __forceinline__ bool rot_params_fast(double a, double b, double gr, double gi, double tol2, double zthr,
-                                                double& cm1, double& sr, double& si) {
+                                                double& cm1, double& sr, double& si, double& tg) {
     const double g2 = gr * gr + gi * gi;
     if (!(a > zthr && b > zthr && g2 / b > tol2 * a)) return false;
     const double gabs = sqrt(g2);
@@ -136,6 +139,7 @@ __device__ __forceinline__ bool rot_params_fast(double a, double b, double gr, d
     const double sv = t / rr;
     sr = sv * (gr / gabs);
     si = sv * (gi / gabs);
+    tg = t * gabs;
     return true;
 }
 
@@ -184,8 +188,8 @@ __device__ __forceinline__ int rotate_reg(C (&xi)[RPL], C* __restrict__ xjs, int
         gr += __shfl_xor_sync(0xffffffffu, gr, o);
         gi += __shfl_xor_sync(0xffffffffu, gi, o);
     }
-    T cm1, sr, si;
-    if (!rot_params_fast(a, b, gr, gi, tol2, zthr, cm1, sr, si)) return 0;
+    T cm1, sr, si, tg;
+    if (!rot_params_fast(a, b, gr, gi, tol2, zthr, cm1, sr, si, tg)) return 0;
     // same single-rounding update as rotate_pair
 #pragma unroll
     for (int k = 0; k < RPL; k += 2) {
@@ -211,6 +215,85 @@ __device__ __forceinline__ int rotate_reg(C (&xi)[RPL], C* __restrict__ xjs, int
         }
     }
     return 1;
+}
+
+// As rotate_reg, with the two column norms tracked instead of recomputed: a (the
+// register column's, in a register) and *bj (the shared column's, in shared memory).
+// Only g = x_i^H x_j is formed; after a rotation the norms are a - t|g| and b + t|g|
+// (the eigenvalues of the pair's 2 x 2 Gram matrix).  The caller recomputes both
+// exactly when a visit starts, so the tracked values drift over at most BC rotations.
+template <typename T, typename C, int RPL, bool FULL>
+__device__ __forceinline__ int rotate_reg_tracked(C (&xi)[RPL], C* __restrict__ xjs, int m, int lane, T tol2, T zthr,
+                                                  T& a, T* bj) {
+    C xj[RPL];
+    T gr = 0, gi = 0;
+#pragma unroll
+    for (int k = 0; k < RPL; k += 2) {
+        const int r = reg_row(lane, k);
+        if (FULL || r < m) {
+            if constexpr (sizeof(C) == 8) {
+                const float4 v = *reinterpret_cast<const float4*>(xjs + r);
+                xj[k].x = v.x; xj[k].y = v.y; xj[k + 1].x = v.z; xj[k + 1].y = v.w;
+            } else {
+                xj[k] = xjs[r];
+                xj[k + 1] = xjs[r + 1];
+            }
+        } else {
+            xj[k].x = 0; xj[k].y = 0; xj[k + 1].x = 0; xj[k + 1].y = 0;
+        }
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const C u = xi[k + e], v = xj[k + e];
+            gr = fma(u.x, v.x, fma(u.y, v.y, gr));
+            gi = fma(u.x, v.y, fma(-u.y, v.x, gi));
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        gr += __shfl_xor_sync(0xffffffffu, gr, o);
+        gi += __shfl_xor_sync(0xffffffffu, gi, o);
+    }
+    const T b = *bj;
+    T cm1, sr, si, tg;
+    if (!rot_params_fast(a, b, gr, gi, tol2, zthr, cm1, sr, si, tg)) return 0;
+    a -= tg;
+    __syncwarp();
+    if (lane == 0) *bj = b + tg;
+#pragma unroll
+    for (int k = 0; k < RPL; k += 2) {
+        const int r = reg_row(lane, k);
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const C u = xi[k + e], v = xj[k + e];
+            C nu, nv;
+            nu.x = u.x + fma(-si, v.y, fma(-sr, v.x, cm1 * u.x));
+            nu.y = u.y + fma(si, v.x, fma(-sr, v.y, cm1 * u.y));
+            nv.x = v.x + fma(-si, u.y, fma(sr, u.x, cm1 * v.x));
+            nv.y = v.y + fma(si, u.x, fma(sr, u.y, cm1 * v.y));
+            xi[k + e] = nu;
+            xj[k + e] = nv;
+        }
+        if (FULL || r < m) {
+            if constexpr (sizeof(C) == 8) {
+                *reinterpret_cast<float4*>(xjs + r) = make_float4(xj[k].x, xj[k].y, xj[k + 1].x, xj[k + 1].y);
+            } else {
+                xjs[r] = xj[k];
+                xjs[r + 1] = xj[k + 1];
+            }
+        }
+    }
+    return 1;
+}
+
+// squared norm of a register column (reg_row layout), summed over the warp
+template <typename T, typename C, int RPL>
+__device__ __forceinline__ T reg_norm2(const C (&x)[RPL]) {
+    T a = 0;
+#pragma unroll
+    for (int k = 0; k < RPL; ++k) a = fma(x[k].x, x[k].x, fma(x[k].y, x[k].y, a));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    return a;
 }
 
 template <typename C>
@@ -262,6 +345,7 @@ k_jacobi(const GateDesc* __restrict__ gd, int n_gates, double tol_in, int max_sw
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* X = reinterpret_cast<C*>(smem_raw);       // [2*BC][m], column-major
     __shared__ int s_g, s_rnd, s_v, s_exit, s_rot, s_vis;
+    __shared__ T s_bn[BC];                       // tracked squared norms of block J's columns
     __shared__ short s_V[kScanTable];            // visits per round of each gate
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -411,13 +495,25 @@ k_jacobi(const GateDesc* __restrict__ gd, int n_gates, double tol_in, int max_sw
                     }
                 }
                 const bool full = (m == 32 * RPL);
+                // exact norms at the start of the cross pairs: a of the register column,
+                // s_bn[w] of block J's column w
+                T a_i = reg_norm2<T, C, RPL>(xi);
+                if (warp < nJ) {
+                    const C* cj = X + (size_t)(BC + warp) * m;
+                    T bn = 0;
+                    for (int r = lane; r < m; r += 32) bn = fma(cj[r].x, cj[r].x, fma(cj[r].y, cj[r].y, bn));
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) bn += __shfl_xor_sync(0xffffffffu, bn, o);
+                    if (lane == 0) s_bn[warp] = bn;
+                }
+                __syncthreads();
                 for (int sft = 0; sft < BC; ++sft) {
                     const int b = (warp + sft) % BC;
                     if (warp < nI && b < nJ) {
                         my_vis += (lane == 0);
                         C* xjs = X + (size_t)(BC + b) * m;
-                        my_rot += full ? rotate_reg<T, C, RPL, true>(xi, xjs, m, lane, tol2, zthr)
-                                       : rotate_reg<T, C, RPL, false>(xi, xjs, m, lane, tol2, zthr);
+                        my_rot += full ? rotate_reg_tracked<T, C, RPL, true>(xi, xjs, m, lane, tol2, zthr, a_i, &s_bn[b])
+                                       : rotate_reg_tracked<T, C, RPL, false>(xi, xjs, m, lane, tol2, zthr, a_i, &s_bn[b]);
                     }
                     __syncthreads();
                 }
