@@ -69,6 +69,26 @@ def dist_setup():
     return world, rank, local
 
 
+def replica_seed(rank: int) -> int:
+    """Every rank simulates its own replica circuit."""
+    return 1000 + int(rank)
+
+
+def replica_reduce(elapsed, units, dist=None, device="cpu"):
+    """Whole-job figures over the replicas: the slowest rank's elapsed time (MAX) and
+    the units all ranks processed (SUM).  dist: torch.distributed or None (one rank);
+    device: where the reduction tensors live (the rank's GPU under NCCL, the CPU under
+    gloo)."""
+    if dist is None:
+        return elapsed, units
+    import torch
+    t = torch.tensor([float(elapsed)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def peaks():
     p = {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "src": "fallback"}
     f = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -238,7 +258,7 @@ def run_ours(args, world, rank, local):
     dev = torch.device("cuda", local)
 
     depth = PRESAT + args.warmup + 2 * args.steps + 2
-    circ = W.brickwork_su4(N_QUBITS, depth, seed=1000 + rank)
+    circ = W.brickwork_su4(N_QUBITS, depth, seed=replica_seed(rank))
     stream = torch.cuda.Stream(device=dev)
     gemm = getattr(T, "TNSIM_GEMM_" + args.gemm.upper())
     m = T.MPS(N_QUBITS, dtype=T.TNSIM_C64, chi_max=CHI, gemm=gemm, stream=stream.cuda_stream)
@@ -307,28 +327,12 @@ def run_ours(args, world, rank, local):
     clocks = clk.stop()
 
     # ---- aggregate over ranks
-    def allmax(x):
-        if not dist:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
-    def allsum(x):
-        if not dist:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        return float(t.item())
-
-    ms_max = allmax(ms)
-    gates_all = allsum(gates_rank)
+    ms_max, gates_all = replica_reduce(ms, gates_rank, dist, dev)
     value = gates_all / (ms_max / 1000.0)
     e2e_obj = None
     if e2e is not None:
         g_e2e, t_e2e, host_layers = e2e
-        t_max = allmax(t_e2e)
-        g_all = allsum(g_e2e)
+        t_max, g_all = replica_reduce(t_e2e, g_e2e, dist, dev)
         h2d = sum(l.n2 * 32 * 8 for l in host_layers) / len(host_layers)
         d2h = sum(l.n2 * 8 for l in host_layers) / len(host_layers)
         e2e_obj = {"value": g_all / t_max, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
