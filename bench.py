@@ -90,11 +90,12 @@ def replica_reduce(elapsed, units, dist=None, device="cpu"):
 
 
 def peaks():
-    p = {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "src": "fallback"}
+    p = {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+         "src": "fallback"}
     f = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(f):
         d = json.load(open(f))
-        p.update({k: d[k] for k in ("hbm_gbs", "sm_max_mhz") if k in d})
+        p.update({k: d[k] for k in ("hbm_gbs", "sm_max_mhz", "bf16_tflops", "bf16_tflops_sustained") if k in d})
         p["src"] = "measured"
     return p
 
@@ -356,6 +357,22 @@ def run_ours(args, world, rank, local):
                 "peak_src": f"derived: 152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz ({pk['src']} max clock)",
                 "algorithmic_flops_per_launch": flops / max(jac_n, 1),
                 "avg_launch_ms": jac_ms / max(jac_n, 1)}
+    # ---- whole-gate roofline time T* (contraction on the tensor pipe at the TF32 rate,
+    # Jacobi and right-site product on the FP32 ALUs, site reads and writes at HBM rate)
+    ng = max(stats["gates"], 1)
+    tf32_peak = pk["bf16_tflops_sustained"] * (1.1 / 2.25)          # nominal TF32 : BF16 dense ratio
+    t_contract = 8.0 * stats["theta_cmacs"] / ng / (tf32_peak * 1e12)
+    t_svd = flops / ng / (peak * 1e12)
+    t_right = 8.0 * stats["right_cmacs"] / ng / (peak * 1e12)
+    site_bytes = 4.0 * 2 * CHI * CHI * 8                             # read A, B; write A', B' (complex64)
+    t_mem = site_bytes / (pk["hbm_gbs"] * 1e9)
+    t_star = t_contract + t_svd + t_right + t_mem
+    path_roofline = {"t_star_us_per_gate": t_star * 1e6, "gates_per_s_at_roofline": 1.0 / t_star,
+                     "frac": value / (1.0 / t_star),
+                     "parts_us": {"contraction_tf32": t_contract * 1e6, "jacobi_fp32": t_svd * 1e6,
+                                  "right_site_fp32": t_right * 1e6, "site_bytes_hbm": t_mem * 1e6},
+                     "peaks": f"TF32 {tf32_peak:.0f} TFLOP/s (measured sustained BF16 x 1.1/2.25), FP32 ALU "
+                              f"{peak:.1f} TFLOP/s, HBM {pk['hbm_gbs']:.0f} GB/s"}
     total_k_ms = sum(v[0] for v in prof.values())
     kernels = {k: {"ms": v[0], "launches": v[1], "share": (v[0] / total_k_ms if total_k_ms else 0.0)}
                for k, v in prof.items() if v[1]}
@@ -467,7 +484,8 @@ def run_ours(args, world, rank, local):
                 "config": cfg, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e_obj,
                 "gpu_launches": launches, "clocks": clocks, "plain_path": plain,
                 "vs_plain": (value / plain["value"]) if plain else None, "kernels": kernels,
-                "nonlocal": nonlocal_obj, "sampling": sampling_obj, "grad": grad_obj}
+                "nonlocal": nonlocal_obj, "sampling": sampling_obj, "grad": grad_obj,
+                "path_roofline": path_roofline}
         print(json.dumps(line), flush=True)
     m.close()
     if dist:

@@ -303,6 +303,24 @@ __device__ __forceinline__ void copy_block_in(C* dst, const C* src, int count) {
     int4* d = reinterpret_cast<int4*>(dst);
     for (int i = threadIdx.x; i < units; i += blockDim.x) d[i] = __ldcg(s + i);
 }
+// Both blocks of a visit into shared memory with asynchronous 16-byte copies
+// (cp.async.cg: through L2, no registers held), so every copy of both blocks is in
+// flight at once; the caller's barrier follows the wait.
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
+template <typename C>
+__device__ __forceinline__ void copy_blocks_in(C* dI, const C* sI, int countI, C* dJ, const C* sJ, int countJ) {
+    const int uI = (int)((size_t)countI * sizeof(C) / 16), uJ = (int)((size_t)countJ * sizeof(C) / 16);
+    const int4* a = reinterpret_cast<const int4*>(sI);
+    const int4* b = reinterpret_cast<const int4*>(sJ);
+    int4* da = reinterpret_cast<int4*>(dI);
+    int4* db = reinterpret_cast<int4*>(dJ);
+    for (int i = threadIdx.x; i < uI; i += blockDim.x) cp_async16(da + i, a + i);
+    for (int i = threadIdx.x; i < uJ; i += blockDim.x) cp_async16(db + i, b + i);
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
 template <typename C>
 __device__ __forceinline__ void copy_block_out(C* dst, const C* src, int count) {
     const int units = (int)((size_t)count * sizeof(C) / 16);
@@ -459,8 +477,8 @@ k_jacobi(const GateDesc* __restrict__ gd, int n_gates, double tol_in, int max_sw
         if (J >= 0 || intra) {
             const int colI = I * BC, nI = min(BC, n - colI);
             const int colJ = J >= 0 ? J * BC : 0, nJ = J >= 0 ? min(BC, n - colJ) : 0;
-            copy_block_in(X, Wm + (size_t)colI * m, nI * m);
-            if (J >= 0) copy_block_in(X + (size_t)BC * m, Wm + (size_t)colJ * m, nJ * m);
+            copy_blocks_in(X, Wm + (size_t)colI * m, nI * m, X + (size_t)BC * m, Wm + (size_t)colJ * m,
+                           J >= 0 ? nJ * m : 0);
             __syncthreads();
             if (intra) {
                 // pairs inside block I (warps 0..BC/2-1) and inside block J (the rest)
