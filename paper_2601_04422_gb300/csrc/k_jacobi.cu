@@ -296,13 +296,6 @@ __device__ __forceinline__ T reg_norm2(const C (&x)[RPL]) {
     return a;
 }
 
-template <typename C>
-__device__ __forceinline__ void copy_block_in(C* dst, const C* src, int count) {
-    const int units = (int)((size_t)count * sizeof(C) / 16);
-    const int4* s = reinterpret_cast<const int4*>(src);
-    int4* d = reinterpret_cast<int4*>(dst);
-    for (int i = threadIdx.x; i < units; i += blockDim.x) d[i] = __ldcg(s + i);
-}
 // Both blocks of a visit into shared memory with asynchronous 16-byte copies
 // (cp.async.cg: through L2, no registers held), so every copy of both blocks is in
 // flight at once; the caller's barrier follows the wait.
@@ -321,12 +314,14 @@ __device__ __forceinline__ void copy_blocks_in(C* dI, const C* sI, int countI, C
     for (int i = threadIdx.x; i < uJ; i += blockDim.x) cp_async16(db + i, b + i);
     asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
+// shared-memory block back to W (L2 stores) by the threads from first_thread on
 template <typename C>
-__device__ __forceinline__ void copy_block_out(C* dst, const C* src, int count) {
+__device__ __forceinline__ void copy_block_out_from(C* dst, const C* src, int count, int first_thread) {
     const int units = (int)((size_t)count * sizeof(C) / 16);
     const int4* s = reinterpret_cast<const int4*>(src);
     int4* d = reinterpret_cast<int4*>(dst);
-    for (int i = threadIdx.x; i < units; i += blockDim.x) __stcg(d + i, s[i]);
+    const int nt = (int)blockDim.x - first_thread;
+    for (int i = (int)threadIdx.x - first_thread; i < units; i += nt) __stcg(d + i, s[i]);
 }
 
 // Geometry of one gate's tournament: nb column blocks, P players (nb rounded up to
@@ -348,6 +343,56 @@ __device__ __forceinline__ Tour tour_of(const GateDesc& d) {
 
 constexpr unsigned kSpinLimit = 1u << 22;   // idle polls without any progress before giving up
 constexpr int kScanTable = 2048;              // gates whose visit count is cached in shared memory
+
+// Warp-parallel claim of one visit (warp 0): each lane checks one gate per pass (one
+// L2 round trip), the first claimable gate in descriptor order from scan0 on is tried
+// with an atomic.  found = 0 when nothing is claimable now.
+template <int BC>
+__device__ __forceinline__ void claim_scan(const GateDesc* __restrict__ gd, int n_gates, const short* s_V, int scan0,
+                                           int lane, int& found, int& fg, int& frnd, int& fv) {
+    found = 0;
+    fg = -1;
+    frnd = 0;
+    fv = 0;
+    const int nchunks = (n_gates + 31) / 32;
+    for (int c = 0; c < nchunks && !found; ++c) {
+        int base = scan0 + 32 * c;
+        if (base >= nchunks * 32) base -= nchunks * 32;
+        const int g = base + lane;
+        bool ok = false;
+        int V = 0;
+        GateOut* o = nullptr;
+        if (g < n_gates) {
+            o = gd[g].out;
+            V = g < kScanTable ? (int)s_V[g] : tour_of<BC>(gd[g]).V;
+            const int fin = *((volatile int*)&o->finished);
+            const unsigned long long cur = *((volatile unsigned long long*)&o->claim);
+            ok = !fin && (unsigned)(cur & 0xffffffffull) < (unsigned)V;
+        }
+        unsigned mask = __ballot_sync(0xffffffffu, ok);
+        while (mask && !found) {
+            const int l = __ffs(mask) - 1;
+            int got = 0;
+            if (lane == l) {
+                const unsigned long long st = atomicAdd(&o->claim, 1ull);
+                if ((unsigned)(st & 0xffffffffull) < (unsigned)V) {
+                    got = 1;
+                    fg = g;
+                    frnd = (int)(st >> 32);
+                    fv = (int)(st & 0xffffffffull);
+                }
+            }
+            got = __shfl_sync(0xffffffffu, got, l);
+            if (got) {
+                fg = __shfl_sync(0xffffffffu, fg, l);
+                frnd = __shfl_sync(0xffffffffu, frnd, l);
+                fv = __shfl_sync(0xffffffffu, fv, l);
+                found = 1;
+            }
+            mask &= mask - 1;
+        }
+    }
+}
 
 // Persistent kernel: every CTA repeatedly claims one visit (gate g, global round
 // number, block pair v) from the gates' claim words, processes it, and reports it.
@@ -375,48 +420,18 @@ k_jacobi(const GateDesc* __restrict__ gd, int n_gates, double tol_in, int max_sw
         s_V[g] = (short)tour_of<BC>(gd[g]).V;
     __syncthreads();
 
+    int have_next = 0, nxt_g = -1, nxt_rnd = 0, nxt_v = 0;   // warp 0: a claim made during the last visit
     for (;;) {
         if (warp == 0) {
-            // warp-parallel scan: each lane checks one gate per pass (one L2 round trip),
-            // the first claimable gate in descriptor order is tried with an atomic
             int found = 0, fg = -1, frnd = 0, fv = 0;
-            const int nchunks = (n_gates + 31) / 32;
-            for (int c = 0; c < nchunks && !found; ++c) {
-                int base = scan0 + 32 * c;
-                if (base >= nchunks * 32) base -= nchunks * 32;
-                const int g = base + lane;
-                bool ok = false;
-                int V = 0;
-                GateOut* o = nullptr;
-                if (g < n_gates) {
-                    o = gd[g].out;
-                    V = g < kScanTable ? (int)s_V[g] : tour_of<BC>(gd[g]).V;
-                    const int fin = *((volatile int*)&o->finished);
-                    const unsigned long long cur = *((volatile unsigned long long*)&o->claim);
-                    ok = !fin && (unsigned)(cur & 0xffffffffull) < (unsigned)V;
-                }
-                unsigned mask = __ballot_sync(0xffffffffu, ok);
-                while (mask && !found) {
-                    const int l = __ffs(mask) - 1;
-                    int got = 0;
-                    if (lane == l) {
-                        const unsigned long long st = atomicAdd(&o->claim, 1ull);
-                        if ((unsigned)(st & 0xffffffffull) < (unsigned)V) {
-                            got = 1;
-                            fg = g;
-                            frnd = (int)(st >> 32);
-                            fv = (int)(st & 0xffffffffull);
-                        }
-                    }
-                    got = __shfl_sync(0xffffffffu, got, l);
-                    if (got) {
-                        fg = __shfl_sync(0xffffffffu, fg, l);
-                        frnd = __shfl_sync(0xffffffffu, frnd, l);
-                        fv = __shfl_sync(0xffffffffu, fv, l);
-                        found = 1;
-                    }
-                    mask &= mask - 1;
-                }
+            if (have_next) {
+                found = 1;
+                fg = nxt_g;
+                frnd = nxt_rnd;
+                fv = nxt_v;
+                have_next = 0;
+            } else {
+                claim_scan<BC>(gd, n_gates, s_V, scan0, lane, found, fg, frnd, fv);
             }
             if (found) scan0 = fg & ~31;
             if (lane == 0) {
@@ -543,8 +558,20 @@ k_jacobi(const GateDesc* __restrict__ gd, int n_gates, double tol_in, int max_sw
                 }
                 __syncthreads();
             }
-            copy_block_out(Wm + (size_t)colI * m, X, nI * m);
-            if (J >= 0) copy_block_out(Wm + (size_t)colJ * m, X + (size_t)BC * m, nJ * m);
+            if (warp > 0) {
+                copy_block_out_from(Wm + (size_t)colI * m, X, nI * m, 32);
+                if (J >= 0) copy_block_out_from(Wm + (size_t)colJ * m, X + (size_t)BC * m, nJ * m, 32);
+            }
+        }
+        // warp 0 claims the next visit while the other warps write the blocks back (a CTA
+        // never waits while holding a claim, so claiming before this visit's report is safe)
+        if (warp == 0) {
+            int found, fg, frnd, fv;
+            claim_scan<BC>(gd, n_gates, s_V, scan0, lane, found, fg, frnd, fv);
+            have_next = found;
+            nxt_g = fg;
+            nxt_rnd = frnd;
+            nxt_v = fv;
         }
         if (lane == 0 && my_rot) atomicAdd(&s_rot, my_rot);
         if (lane == 0 && my_vis) atomicAdd(&s_vis, my_vis);
