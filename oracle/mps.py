@@ -18,7 +18,7 @@ The two-qubit update follows Sec. III.A "Two Qubit Gate" and Sec. III.B
    singular vectors with the singular values contracted in become the right
    ("target") site (Sec. III.A "Two Qubit Gate").
 
-Readings where the paper is silent (each one is also listed in the design doc):
+Readings where the paper is silent:
 
 * truncation rank: singular values below ``eps * max(m, n) * s_max`` are treated
   as exact zeros; then k = min(chi_max, #nonzero, smallest k whose discarded
