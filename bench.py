@@ -357,20 +357,23 @@ def run_ours(args, world, rank, local):
                 "peak_src": f"derived: 152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz ({pk['src']} max clock)",
                 "algorithmic_flops_per_launch": flops / max(jac_n, 1),
                 "avg_launch_ms": jac_ms / max(jac_n, 1)}
-    # ---- whole-gate roofline time T* (contraction on the tensor pipe at the TF32 rate,
-    # Jacobi and right-site product on the FP32 ALUs, site reads and writes at HBM rate)
+    # ---- whole-gate roofline time T* (contraction on the tensor pipe at the TF32 rate;
+    # QR preconditioning, Jacobi and site product on the FP32 ALUs; site reads and writes
+    # at HBM rate)
     ng = max(stats["gates"], 1)
     tf32_peak = pk["bf16_tflops_sustained"] * (1.1 / 2.25)          # nominal TF32 : BF16 dense ratio
     t_contract = 8.0 * stats["theta_cmacs"] / ng / (tf32_peak * 1e12)
     t_svd = flops / ng / (peak * 1e12)
     t_right = 8.0 * stats["right_cmacs"] / ng / (peak * 1e12)
+    t_qr = 8.0 * stats["qr_cmacs"] / ng / (peak * 1e12)
     site_bytes = 4.0 * 2 * CHI * CHI * 8                             # read A, B; write A', B' (complex64)
     t_mem = site_bytes / (pk["hbm_gbs"] * 1e9)
-    t_star = t_contract + t_svd + t_right + t_mem
+    t_star = t_contract + t_qr + t_svd + t_right + t_mem
     path_roofline = {"t_star_us_per_gate": t_star * 1e6, "gates_per_s_at_roofline": 1.0 / t_star,
                      "frac": value / (1.0 / t_star),
-                     "parts_us": {"contraction_tf32": t_contract * 1e6, "jacobi_fp32": t_svd * 1e6,
-                                  "right_site_fp32": t_right * 1e6, "site_bytes_hbm": t_mem * 1e6},
+                     "parts_us": {"contraction_tf32": t_contract * 1e6, "qr_fp32": t_qr * 1e6,
+                                  "jacobi_fp32": t_svd * 1e6, "site_product_fp32": t_right * 1e6,
+                                  "site_bytes_hbm": t_mem * 1e6},
                      "peaks": f"TF32 {tf32_peak:.0f} TFLOP/s (measured sustained BF16 x 1.1/2.25), FP32 ALU "
                               f"{peak:.1f} TFLOP/s, HBM {pk['hbm_gbs']:.0f} GB/s"}
     total_k_ms = sum(v[0] for v in prof.values())
@@ -473,7 +476,9 @@ def run_ours(args, world, rank, local):
         cfg["parallelism"] = f"replicas x{world}" if world > 1 else "single GPU"
         cfg["jacobi_sweeps_per_gate"] = stats["sweeps"] / max(stats["gates"], 1)
         cfg["jacobi_config"] = {"chosen": int(tune_choice), "autotune_ms": [float(x) for x in tune_ms],
-                                "configs": ["16-column blocks, 1 CTA/SM", "8-column blocks, 2 CTAs/SM"]}
+                                "configs": ["16-column blocks, 1 CTA/SM", "8-column blocks, 2 CTAs/SM",
+                                            "16-column blocks, 1 CTA/SM, QR-preconditioned",
+                                            "8-column blocks, 2 CTAs/SM, QR-preconditioned"]}
         cfg["interior_chi"] = int(np.max(dims))
         cfg["contraction"] = {"fp32": "FP32 FMA (4M)", "fp32_3m": "FP32 FMA (3M)",
                               "tf32x3": "tcgen05 3xTF32, FP32 accumulate",

@@ -259,20 +259,27 @@ tnsim_status tnsim_expect_pauli(tnsim_mps* m, int32_t n_terms, const char* pauli
 tnsim_status tnsim_sample(tnsim_mps* m, int64_t n_shots, const double* uniforms, uint8_t* bits_out,
                           int64_t* n_nodes_out);
 
-/* Launch configurations of the Jacobi SVD: 0 -- 16-column blocks (8 for complex128
- * at chi > 128), one persistent CTA per SM; 1 -- half-width blocks, two CTAs per SM
- * (barriers of the two CTAs are independent; a sweep has twice the rounds). */
-#define TNSIM_JACOBI_CONFIGS 2
+/* Launch configurations of the Jacobi SVD.  Bit 0: 0 -- 16-column blocks (8 for
+ * complex128 at chi > 128), one persistent CTA per SM; 1 -- half-width blocks, two
+ * CTAs per SM (barriers of the two CTAs are independent; a sweep has twice the
+ * rounds).  Bit 1: QR preconditioning (Drmac and Veselic 2008) of every gate whose
+ * gated block is square (2 chi_L == 2 chi_R <= 1536) in the paper's form: theta = Q R
+ * by blocked Householder reflections, the Jacobi iteration runs on the columns of
+ * R^H (fewer sweeps), the left site is theta V S^-1 and the right site S V^H is read
+ * off the converged columns; Q is never formed.  Same kept spectrum and state up to
+ * the Jacobi tolerance. */
+#define TNSIM_JACOBI_CONFIGS 4
 
-/* Use Jacobi configuration cfg (0 or 1) for the later launches of m.
- * Errors: EINVAL. */
+/* Use Jacobi configuration cfg (0 .. TNSIM_JACOBI_CONFIGS - 1) for the later
+ * launches of m.  Errors: EINVAL. */
 tnsim_status tnsim_set_jacobi_config(tnsim_mps* m, int32_t cfg);
 
 /* Autotuner of the Jacobi SVD: contract the given layer (n2 >= 1 pairs q, gates
  * g4x4 on the host, as in tnsim_apply_layer) of the current state into the work
  * space, then time the persistent Jacobi launch of that layer in every
- * configuration (CUDA events on m's stream; W and the gate records are restored
- * before each launch; the best of reps runs is kept), pick the fastest for m's
+ * configuration (CUDA events on m's stream, the QR factorisation included where
+ * the configuration has it; W and the gate records are restored before each
+ * launch; the best of reps runs is kept), pick the fastest for m's
  * later launches and report it in *choice_out (may be NULL); ms_out (may be NULL)
  * receives TNSIM_JACOBI_CONFIGS times in milliseconds.  The state is not changed.
  * Synchronous.  Errors: EINVAL (bad layer, reps outside [1, 100]), ECUDA. */
@@ -334,7 +341,11 @@ typedef struct {
     int64_t visit_rows;    /* sum over examined pairs of m */
     int64_t rotation_rows; /* sum over rotated pairs of m */
     int64_t theta_cmacs;   /* complex multiply-adds of the merge (2chi_L chi_M 2chi_R per gate) */
-    int64_t right_cmacs;   /* complex multiply-adds of the right site (k 2chi_L 2chi_R per gate) */
+    int64_t right_cmacs;   /* complex multiply-adds of the site product: the right site
+                              (k 2chi_L 2chi_R per gate), or with QR preconditioning the
+                              left site (same count) */
+    int64_t qr_cmacs;      /* complex multiply-adds of the QR preconditioning, Householder's
+                              count 2 n^3 / 3 per preconditioned n x n gate block */
 } tnsim_stats;
 
 /* Read (and reset) the counters.  Synchronises.  Errors: EINVAL. */
@@ -342,7 +353,7 @@ tnsim_status tnsim_last_stats(tnsim_mps* m, tnsim_stats* out);
 
 /* Kernel classes timed by the optional profiler, in launch order within a layer. */
 enum { TNSIM_K_SITE1Q = 0, TNSIM_K_THETA = 1, TNSIM_K_JACOBI = 2, TNSIM_K_TRUNCATE = 3,
-       TNSIM_K_LEFT = 4, TNSIM_K_RIGHT = 5, TNSIM_K_COUNT = 6 };
+       TNSIM_K_LEFT = 4, TNSIM_K_RIGHT = 5, TNSIM_K_QR = 6, TNSIM_K_COUNT = 7 };
 
 /* Enable (on != 0) or disable per-kernel timing: while enabled every layer records
  * CUDA events on the handle's stream around each of its kernel launches (no extra

@@ -89,10 +89,10 @@ _sig("tnsim_grad", C.c_int, [C.POINTER(tnsim_circuit), _DP, C.POINTER(tnsim_hami
                              C.POINTER(tnsim_params), _P, _DP, _DP])
 class tnsim_stats(C.Structure):
     _fields_ = [(k, C.c_int64) for k in ("gates", "sweeps", "rotations", "pair_visits", "visit_rows",
-                                          "rotation_rows", "theta_cmacs", "right_cmacs")]
+                                          "rotation_rows", "theta_cmacs", "right_cmacs", "qr_cmacs")]
 
 
-TNSIM_K_NAMES = ["site1q", "theta", "jacobi", "truncate", "left", "right"]
+TNSIM_K_NAMES = ["site1q", "theta", "jacobi", "truncate", "left", "right", "qr"]
 
 _sig("tnsim_last_stats", C.c_int, [_P, C.POINTER(tnsim_stats)])
 _sig("tnsim_profile_enable", C.c_int, [_P, C.c_int32])
@@ -339,7 +339,7 @@ def tnsim_sample(h, uniforms):
     return bits, nodes.value
 
 
-TNSIM_JACOBI_CONFIGS = 2
+TNSIM_JACOBI_CONFIGS = 4
 
 
 def tnsim_set_jacobi_config(h, cfg: int):

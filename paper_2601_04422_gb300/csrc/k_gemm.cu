@@ -190,6 +190,7 @@ __global__ void __launch_bounds__(256) k_right(const GateDesc* __restrict__ gd) 
     const int chiL = d.chi[q], chiR = d.chi[q + 2];
     const int k = d.out->k;
     const int m = 2 * chiL, n = 2 * chiR;
+    if (qr_active(d, m, n)) return;   // QR-preconditioned: k_right_pre (k_qr.cu)
     const int c0 = blockIdx.x * RT_C, j0 = blockIdx.y * RT_J;
     if (c0 >= n || j0 >= k) return;
 

@@ -640,12 +640,13 @@ static cudaError_t launch_bc(const GateDesc* d, int n_gates, int m_max, int n_ma
 // staged blocks take 2 BC m_max elements of shared memory (at most 128 KB).  Two
 // configurations per shape: cfg 0 -- wide blocks, one CTA per SM (fewer rounds per
 // sweep); cfg 1 -- half-width blocks, two CTAs per SM (independent barriers, twice
-// the rounds).  tnsim_autotune times both on a real layer.
+// the rounds).  Bit 1 of a state's configuration (QR preconditioning, k_qr.cu) does not
+// change this launch.  tnsim_autotune times every configuration on a real layer.
 template <typename T>
 cudaError_t launch_jacobi(const GateDesc* d, int n_gates, int m_max, int n_max, double tol,
                           int max_sweeps, JacobiCtl* ctl, cudaStream_t s, int cfg) {
     if (n_gates <= 0) return cudaSuccess;
-    const bool narrow = cfg == 1;
+    const bool narrow = (cfg & 1) != 0;
 #define TNSIM_JAC(BC, RPL, MINB) launch_bc<T, BC, RPL, MINB>(d, n_gates, m_max, n_max, tol, max_sweeps, ctl, s)
     if (m_max <= 64) return narrow ? TNSIM_JAC(8, 2, 2) : TNSIM_JAC(16, 2, 1);
     if (m_max <= 128) return narrow ? TNSIM_JAC(8, 4, 2) : TNSIM_JAC(16, 4, 1);

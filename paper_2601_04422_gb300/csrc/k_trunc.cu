@@ -129,6 +129,7 @@ __global__ void __launch_bounds__(TR_THREADS) k_truncate(const GateDesc* __restr
         atomicAdd(&d.stats[5], out->rotations * (u64)m);
         atomicAdd(&d.stats[6], (u64)m * (u64)chiM * (u64)n);
         atomicAdd(&d.stats[7], (u64)k * (u64)m * (u64)n);
+        if (qr_active(d, m, n)) atomicAdd(&d.stats[8], (u64)2 * (u64)n * (u64)n * (u64)n / 3);
     }
     __syncthreads();
     const int k = s_k;
@@ -156,6 +157,7 @@ __global__ void __launch_bounds__(256) k_left(const GateDesc* __restrict__ gd) {
     const int q = d.q;
     const int chiL = d.chi[q];
     const int m = 2 * chiL;
+    if (qr_active(d, m, 2 * d.chi[q + 2])) return;   // QR-preconditioned: k_left_pre (k_qr.cu)
     const int k = d.out->k;
     const int row0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
     if (row0 >= m || j0 >= k) return;

@@ -83,7 +83,7 @@ struct tnsim_mps {
     Site1Desc* d_s1 = nullptr;     // n
     double* d_gates = nullptr;     // G*32 + n*8
     int* d_sticky = nullptr;
-    unsigned long long* d_stats = nullptr;   // 8 counters (tnsim_stats)
+    unsigned long long* d_stats = nullptr;   // the counters of tnsim_stats
     JacobiCtl* d_ctl = nullptr;    // control word of the persistent Jacobi launch
     int jac_cfg = 0;               // Jacobi launch configuration (tnsim_set_jacobi_config / tnsim_autotune)
     // tensor-core contraction (complex64 with gemm TF32X3 / BF16X3)
@@ -117,6 +117,7 @@ struct tnsim_plan {
     Site1Desc* d_s1 = nullptr;
     JacobiCtl* d_ctl = nullptr;
     bool canon = false;            // some state of the plan is in canonical form
+    bool qr = false;               // some state of the plan selected QR preconditioning
     int jac_cfg = 0;               // Jacobi launch configuration of the first state
 };
 
@@ -242,8 +243,9 @@ struct GateJob {
 };
 
 // Fill and upload the descriptors of a batch of gates (possibly from several states).
+// qr_force >= 0 replaces every state's QR-preconditioning choice (the autotuner's descriptors).
 tnsim_status upload_desc(cudaStream_t st, const std::vector<GateJob>& jobs, GateDesc* h_desc,
-                         GateDesc* d_desc, GateOut* d_out_base) {
+                         GateDesc* d_desc, GateOut* d_out_base, int qr_force = -1) {
     const int ng = (int)jobs.size();
     if (ng == 0) return TNSIM_OK;
     for (int i = 0; i < ng; ++i) {
@@ -282,6 +284,7 @@ tnsim_status upload_desc(cudaStream_t st, const std::vector<GateJob>& jobs, Gate
         d.canon = m->p.form == TNSIM_FORM_CANONICAL ? 1 : 0;
         d.lam = m->d_spec + (size_t)j.q * m->p.chi_max;
         d.lam_k = m->d_spec_k + j.q;
+        d.qr = qr_force >= 0 ? qr_force : (m->jac_cfg >> 1) & 1;
     }
     CUDA_TRY(cudaMemcpyAsync(d_desc, h_desc, sizeof(GateDesc) * ng, cudaMemcpyHostToDevice, st));
     return TNSIM_OK;
@@ -310,10 +313,18 @@ tnsim_status launch_gates(cudaStream_t st, const std::vector<GateJob>& jobs, con
         CUDA_TRY(launch_theta_tc(pm->tc_mode, d_desc, ng, chiL_max, chiM_max, chiR_max, st));
     }
     prof_end(pm, st, TNSIM_K_THETA, ev);
-    bool canon = false;
-    for (const GateJob& j : jobs) canon = canon || j.m->p.form == TNSIM_FORM_CANONICAL;
+    bool canon = false, qr = false;
+    for (const GateJob& j : jobs) {
+        canon = canon || j.m->p.form == TNSIM_FORM_CANONICAL;
+        qr = qr || (j.m->jac_cfg & 2) != 0;
+    }
     if (canon) CUDA_TRY(launch_scale_rows<T>(d_desc, ng, st));
     CUDA_TRY(cudaMemsetAsync(pm->d_ctl, 0, sizeof(JacobiCtl), st));
+    if (qr) {
+        ev = prof_begin(pm, st);
+        CUDA_TRY(launch_qr<T>(d_desc, ng, m_max, st));
+        prof_end(pm, st, TNSIM_K_QR, ev);
+    }
     ev = prof_begin(pm, st);
     CUDA_TRY(launch_jacobi<T>(d_desc, ng, m_max, n_max, tol, sweeps, pm->d_ctl, st, pm->jac_cfg));
     prof_end(pm, st, TNSIM_K_JACOBI, ev);
@@ -326,6 +337,7 @@ tnsim_status launch_gates(cudaStream_t st, const std::vector<GateJob>& jobs, con
     ev = prof_begin(pm, st);
     CUDA_TRY(launch_right<T>(d_desc, ng, k_max, n_max, st));
     if (canon) CUDA_TRY(launch_left_canon<T>(d_desc, ng, m_max, k_max, st));
+    if (qr) CUDA_TRY(launch_sites_pre<T>(d_desc, ng, m_max, k_max, n_max, st));
     prof_end(pm, st, TNSIM_K_RIGHT, ev);
     // bounds for the next layer
     for (const GateJob& j : jobs) {
@@ -523,7 +535,7 @@ tnsim_status tnsim_mps_create(int32_t n_qubits, tnsim_dtype dt, const tnsim_para
     ALLOC(m->d_s1, (size_t)n_qubits * sizeof(Site1Desc));
     ALLOC(m->d_gates, gate_doubles * sizeof(double));
     ALLOC(m->d_sticky, sizeof(int));
-    ALLOC(m->d_stats, 8 * sizeof(unsigned long long));
+    ALLOC(m->d_stats, sizeof(tnsim_stats));
     ALLOC(m->d_ctl, sizeof(JacobiCtl));
     HALLOC(m->h_out, nG * sizeof(GateOut));
     HALLOC(m->h_chi, sizeof(int) * (n_qubits + 1));
@@ -575,7 +587,7 @@ tnsim_status tnsim_mps_create(int32_t n_qubits, tnsim_dtype dt, const tnsim_para
     if (e == cudaSuccess) e = cudaMemcpy(m->d_chi, ones.data(), sizeof(int) * (n_qubits + 1), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(m->d_spec_k, 0, sizeof(int) * (n_qubits + 1));
     if (e == cudaSuccess) e = cudaMemset(m->d_sticky, 0, sizeof(int));
-    if (e == cudaSuccess) e = cudaMemset(m->d_stats, 0, 8 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(m->d_stats, 0, sizeof(tnsim_stats));
     if (e == cudaSuccess) e = cudaMemset(m->d_out, 0, nG * sizeof(GateOut));
     if (e != cudaSuccess) {
         free_all(m); delete m;
@@ -887,6 +899,7 @@ tnsim_status tnsim_plan_create(tnsim_mps* const* ms, int32_t n_states, const int
     p->gemm = m0->p.gemm;
     for (int i = 0; i < n_states; ++i) p->canon = p->canon || ms[i]->p.form == TNSIM_FORM_CANONICAL;
     p->jac_cfg = m0->jac_cfg;
+    for (int i = 0; i < n_states; ++i) p->qr = p->qr || (ms[i]->jac_cfg & 2) != 0;
     p->tc_mode = m0->tc_mode;
     p->tol = m0->p.jacobi_tol;
     std::vector<GateJob> jobs;
@@ -971,21 +984,25 @@ tnsim_status tnsim_plan_launch(tnsim_plan* p) {
     if (p->dt == TNSIM_C128) {
         CUDA_TRY(launch_theta<double>(p->d_desc, ng, p->chiL_max, p->chiR_max, st));
         if (p->canon) CUDA_TRY(launch_scale_rows<double>(p->d_desc, ng, st));
+        if (p->qr) CUDA_TRY(launch_qr<double>(p->d_desc, ng, m_max, st));
         CUDA_TRY(launch_jacobi<double>(p->d_desc, ng, m_max, n_max, p->tol, p->sweeps, p->d_ctl, st, p->jac_cfg));
         CUDA_TRY(launch_truncate<double>(p->d_desc, ng, st));
         CUDA_TRY(launch_left<double>(p->d_desc, ng, m_max, p->k_max, st));
         CUDA_TRY(launch_right<double>(p->d_desc, ng, p->k_max, n_max, st));
         if (p->canon) CUDA_TRY(launch_left_canon<double>(p->d_desc, ng, m_max, p->k_max, st));
+        if (p->qr) CUDA_TRY(launch_sites_pre<double>(p->d_desc, ng, m_max, p->k_max, n_max, st));
     } else {
         if (p->gemm == TNSIM_GEMM_FP32) CUDA_TRY(launch_theta<float>(p->d_desc, ng, p->chiL_max, p->chiR_max, st));
         else if (p->gemm == TNSIM_GEMM_FP32_3M) CUDA_TRY(launch_theta_3m(p->d_desc, ng, p->chiL_max, p->chiR_max, st));
         else CUDA_TRY(launch_theta_tc(p->tc_mode, p->d_desc, ng, p->chiL_max, p->chiM_max, p->chiR_max, st));
         if (p->canon) CUDA_TRY(launch_scale_rows<float>(p->d_desc, ng, st));
+        if (p->qr) CUDA_TRY(launch_qr<float>(p->d_desc, ng, m_max, st));
         CUDA_TRY(launch_jacobi<float>(p->d_desc, ng, m_max, n_max, p->tol, p->sweeps, p->d_ctl, st, p->jac_cfg));
         CUDA_TRY(launch_truncate<float>(p->d_desc, ng, st));
         CUDA_TRY(launch_left<float>(p->d_desc, ng, m_max, p->k_max, st));
         CUDA_TRY(launch_right<float>(p->d_desc, ng, p->k_max, n_max, st));
         if (p->canon) CUDA_TRY(launch_left_canon<float>(p->d_desc, ng, m_max, p->k_max, st));
+        if (p->qr) CUDA_TRY(launch_sites_pre<float>(p->d_desc, ng, m_max, p->k_max, n_max, st));
     }
     // the bond upper bounds the host keeps become the capacities
     for (tnsim_mps* m : p->states)
@@ -1357,7 +1374,7 @@ tnsim_status tnsim_autotune(tnsim_mps* m, int32_t n2, const int32_t* q, const do
     CUDA_TRY(cudaMemcpyAsync(m->d_gates, stg->gates, sizeof(double) * 32 * n2, cudaMemcpyHostToDevice, st));
     std::vector<GateJob> jobs = layer_jobs(m, n2, q, m->d_gates, nullptr, nullptr);
     CUDA_TRY(cudaMemsetAsync(m->d_out, 0, sizeof(GateOut) * n2, st));
-    s = upload_desc(st, jobs, stg->desc, m->d_desc, nullptr);
+    s = upload_desc(st, jobs, stg->desc, m->d_desc, nullptr, 1);
     CUDA_TRY(cudaEventRecord(stg->done, st));
     if (s != TNSIM_OK) return s;
     int chiL_max = 1, chiM_max = 1, chiR_max = 1;
@@ -1404,6 +1421,9 @@ tnsim_status tnsim_autotune(tnsim_mps* m, int32_t n2, const int32_t* q, const do
                                     cudaMemcpyDeviceToDevice, st);
             if (e == cudaSuccess) e = cudaMemsetAsync(m->d_ctl, 0, sizeof(JacobiCtl), st);
             if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+            if (e == cudaSuccess && (c & 2))
+                e = m->dt == TNSIM_C64 ? launch_qr<float>(m->d_desc, n2, m_max, st)
+                                       : launch_qr<double>(m->d_desc, n2, m_max, st);
             if (e == cudaSuccess)
                 e = m->dt == TNSIM_C64
                         ? launch_jacobi<float>(m->d_desc, n2, m_max, n_max, default_tol(m), default_sweeps(m), m->d_ctl, st, c)
@@ -1766,7 +1786,8 @@ tnsim_status tnsim_last_stats(tnsim_mps* m, tnsim_stats* out) {
     if (!m || !out) return fail(TNSIM_EINVAL, "NULL argument");
     DevGuard g(m->device);
     CUDA_TRY(cudaStreamSynchronize(m->stream));
-    unsigned long long st[8];
+    unsigned long long st[9];
+    static_assert(sizeof(st) == sizeof(tnsim_stats), "one device counter per tnsim_stats field");
     CUDA_TRY(cudaMemcpy(st, m->d_stats, sizeof(st), cudaMemcpyDeviceToHost));
     CUDA_TRY(cudaMemset(m->d_stats, 0, sizeof(st)));
     out->gates = (int64_t)st[0];
@@ -1777,6 +1798,7 @@ tnsim_status tnsim_last_stats(tnsim_mps* m, tnsim_stats* out) {
     out->rotation_rows = (int64_t)st[5];
     out->theta_cmacs = (int64_t)st[6];
     out->right_cmacs = (int64_t)st[7];
+    out->qr_cmacs = (int64_t)st[8];
     return TNSIM_OK;
 }
 

@@ -55,7 +55,8 @@ struct GateDesc {
     double* eps_out;      // optional copy of the discarded weight (device), or null
     GateOut* out;
     int* sticky;          // the state's sticky status word (OR of gate statuses)
-    unsigned long long* stats;  // the state's 8 work counters (layout of tnsim_stats)
+    unsigned long long* stats;  // the state's work counters (layout of tnsim_stats; the last one, qr_cmacs,
+                                // only for QR-preconditioned gates)
     // split operand planes for the tensor-core contraction (complex64, TF32X3 / BF16X3)
     void* tc_planes;      // this state's plane buffer [slots * 8][tc_rows][tc_k]
     const void* tc_map_a; // CUtensorMap over the planes, 128-row boxes (device memory)
@@ -72,7 +73,19 @@ struct GateDesc {
     int canon;
     const double* lam;    // singular values of bond q (the state's spectrum of bond q)
     const int* lam_k;     // their count (0 = bond never decomposed: all ones)
+    // QR preconditioning (k_qr.cu): for m == n the Jacobi runs on R^H of theta = Q R; the
+    // left site becomes theta W' S^-2 and the right site the conjugated Jacobi columns
+    int qr;
+    int pad_;
 };
+
+// largest m of a QR-preconditioned gate (its panel of columns sits in shared memory)
+constexpr int kQrMaxRows = 1536;
+#ifdef __CUDACC__
+__device__ __forceinline__ bool qr_active(const GateDesc& d, int m, int n) {
+    return d.qr && !d.canon && m == n && m <= kQrMaxRows;
+}
+#endif
 
 // One-qubit update of one site (Eq. 3).
 struct Site1Desc {
@@ -88,8 +101,9 @@ template <typename T>
 cudaError_t launch_theta(const GateDesc* d, int n_gates, int chiL_max, int chiR_max,
                          cudaStream_t s);
 // cfg selects the block width / CTAs per SM (0: wide blocks, 1 CTA per SM; 1: half-width
-// blocks, 2 CTAs per SM); kJacobiConfigs of them.
-constexpr int kJacobiConfigs = 2;
+// blocks, 2 CTAs per SM).  The configurations a state can select add QR preconditioning
+// (bit 1 of the state's configuration, GateDesc::qr): kJacobiConfigs of them.
+constexpr int kJacobiConfigs = 4;
 template <typename T>
 cudaError_t launch_jacobi(const GateDesc* d, int n_gates, int m_max, int n_max, double tol,
                           int max_sweeps, JacobiCtl* ctl, cudaStream_t s, int cfg = 0);
@@ -105,6 +119,12 @@ template <typename T>
 cudaError_t launch_scale_rows(const GateDesc* d, int n_gates, cudaStream_t s);
 template <typename T>
 cudaError_t launch_left_canon(const GateDesc* d, int n_gates, int m_max, int k_max, cudaStream_t s);
+// QR preconditioning: W <- R^H of theta = Q R for every gate with qr_active; after the
+// truncation, the left and right sites of those gates from the Jacobi columns
+template <typename T>
+cudaError_t launch_qr(const GateDesc* d, int n_gates, int m_max, cudaStream_t s);
+template <typename T>
+cudaError_t launch_sites_pre(const GateDesc* d, int n_gates, int m_max, int k_max, int n_max, cudaStream_t s);
 template <typename T>
 cudaError_t launch_site1q(const Site1Desc* d, int n_sites, int cap_lr, cudaStream_t s);
 

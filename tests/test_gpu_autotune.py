@@ -1,8 +1,9 @@
 """The Jacobi launch configurations and their autotuner (tnsim_autotune).
 
-Every configuration must give the oracle's results (they only change the block
-width, hence the order of the rotations); the autotuner must leave the state
-exactly as it was and pick one of them.
+Every configuration must give the oracle's results (they change the block width,
+hence the order of the rotations, and whether the Jacobi iteration runs on theta or
+on R^H of its QR factorisation); the autotuner must leave the state exactly as it
+was and pick one of them.
 """
 import numpy as np
 import pytest
@@ -26,7 +27,7 @@ def _all_bits(n):
     return np.array([[(x >> (n - 1 - i)) & 1 for i in range(n)] for x in range(2 ** n)], dtype=np.uint8)
 
 
-@pytest.mark.parametrize("cfg", [0, 1])
+@pytest.mark.parametrize("cfg", [0, 1, 2, 3])
 def test_every_configuration_exact_complex128(T, cfg):
     circ, p = W.config_c1(2)
     m = T.MPS(10, dtype=T.TNSIM_C128, chi_max=p["chi_max"])
@@ -38,7 +39,7 @@ def test_every_configuration_exact_complex128(T, cfg):
     m.close()
 
 
-@pytest.mark.parametrize("cfg", [0, 1])
+@pytest.mark.parametrize("cfg", [0, 1, 2, 3])
 def test_every_configuration_complex64_per_layer(T, cfg):
     """24 qubits, chi 64 (m up to 128): every layer against the oracle on the same input."""
     circ = W.brickwork_u2_su4(24, 9, seed=6)
@@ -63,7 +64,7 @@ def test_autotune_keeps_the_state_and_picks_a_configuration(T):
     dims = list(m.bond_dims())
     lay = circ.layers[8]
     choice, ms = T.tnsim_autotune(m.h, lay.pairs, lay.g4, reps=2)
-    assert choice in (0, 1) and np.all(ms > 0) and ms[choice] == ms.min()
+    assert choice in range(T.TNSIM_JACOBI_CONFIGS) and len(ms) == 4 and np.all(ms > 0) and ms[choice] == ms.min()
     assert list(m.bond_dims()) == dims
     for a, b in zip(m.export_sites(), before):
         assert np.array_equal(a, b)
@@ -74,5 +75,5 @@ def test_autotune_keeps_the_state_and_picks_a_configuration(T):
         sg = m.spectrum(r.q + 1)
         assert len(sg) == r.k and np.max(np.abs(sg - r.s_kept)) / r.s_kept[0] <= 1e-5
     with pytest.raises(T.TnsimError):
-        T.tnsim_set_jacobi_config(m.h, 2)
+        T.tnsim_set_jacobi_config(m.h, 4)
     m.close()
