@@ -113,7 +113,8 @@ __global__ void __launch_bounds__(QT, 1) k_qr(const GateDesc* __restrict__ gd) {
 
     for (int p0 = 0; p0 < n; p0 += NB) {
         const int nbp = min(NB, n - p0), L0 = m - p0;
-        // ---- panel into shared memory (written by every CTA of the cluster in the last round)
+        // ---- panel into shared memory (its columns were last written by the previous panel's
+        // trailing update, possibly in another CTA of the cluster)
         for (int c = warp; c < NB; c += QW) {
             C* dst = Vp + (size_t)c * L0;
             if (c < nbp) {
