@@ -345,8 +345,8 @@ constexpr unsigned kSpinLimit = 1u << 22;   // idle polls without any progress b
 constexpr int kScanTable = 2048;              // gates whose visit count is cached in shared memory
 
 // Warp-parallel claim of one visit (warp 0): each lane checks one gate per pass (one
-// L2 round trip), the first claimable gate in descriptor order from scan0 on is tried
-// with an atomic.  found = 0 when nothing is claimable now.
+// L2 round trip), the first claimable gate in descriptor order from gate scan0 on
+// (wrapping around) is tried with an atomic.  found = 0 when nothing is claimable now.
 template <int BC>
 __device__ __forceinline__ void claim_scan(const GateDesc* __restrict__ gd, int n_gates, const short* s_V, int scan0,
                                            int lane, int& found, int& fg, int& frnd, int& fv) {
@@ -356,9 +356,8 @@ __device__ __forceinline__ void claim_scan(const GateDesc* __restrict__ gd, int 
     fv = 0;
     const int nchunks = (n_gates + 31) / 32;
     for (int c = 0; c < nchunks && !found; ++c) {
-        int base = scan0 + 32 * c;
-        if (base >= nchunks * 32) base -= nchunks * 32;
-        const int g = base + lane;
+        const int k = 32 * c + lane;
+        const int g = k < n_gates ? (scan0 + k) % n_gates : n_gates;   // every gate once
         bool ok = false;
         int V = 0;
         GateOut* o = nullptr;
@@ -402,7 +401,7 @@ __device__ __forceinline__ void claim_scan(const GateDesc* __restrict__ gd, int 
 // a CTA with nothing to claim only waits for work that running CTAs are doing.
 template <typename T, int BC, int RPL, int MINB>
 __global__ void __launch_bounds__(BC * 32, MINB)
-k_jacobi(const GateDesc* __restrict__ gd, int n_gates, double tol_in, int max_sweeps,
+k_jacobi(const GateDesc* __restrict__ gd, int n_gates, int n_lead, double tol_in, int max_sweeps,
          JacobiCtl* __restrict__ ctl) {
     using C = typename CT<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -413,9 +412,11 @@ k_jacobi(const GateDesc* __restrict__ gd, int n_gates, double tol_in, int max_sw
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned spins = 0, last_progress = 0;
-    // where this CTA starts scanning: the front (largest gates) when the gates are few,
-    // a spread-out offset when they are many; afterwards the last gate it claimed
-    int scan0 = (n_gates > 2 * (int)gridDim.x) ? (int)(((long long)blockIdx.x * n_gates) / gridDim.x) & ~31 : 0;
+    // where this CTA starts scanning: spread over the n_lead leading gates (those as large
+    // as the first; the descriptors come sorted by decreasing size), so the CTAs share out
+    // the largest gates instead of crowding the first ones; afterwards the gate it last
+    // claimed, and from there on in descriptor order
+    int scan0 = (int)(((long long)blockIdx.x * n_lead) / gridDim.x);
     for (int g = threadIdx.x; g < n_gates && g < kScanTable; g += blockDim.x)
         s_V[g] = (short)tour_of<BC>(gd[g]).V;
     __syncthreads();
@@ -433,7 +434,7 @@ k_jacobi(const GateDesc* __restrict__ gd, int n_gates, double tol_in, int max_sw
             } else {
                 claim_scan<BC>(gd, n_gates, s_V, scan0, lane, found, fg, frnd, fv);
             }
-            if (found) scan0 = fg & ~31;
+            if (found) scan0 = fg;
             if (lane == 0) {
                 s_exit = 0;
                 s_g = found ? fg : -1;
@@ -612,7 +613,7 @@ k_jacobi(const GateDesc* __restrict__ gd, int n_gates, double tol_in, int max_sw
 }
 
 template <typename T, int BC, int RPL, int MINB>
-static cudaError_t launch_bc(const GateDesc* d, int n_gates, int m_max, int n_max, double tol,
+static cudaError_t launch_bc(const GateDesc* d, int n_gates, int n_lead, int m_max, int n_max, double tol,
                              int max_sweeps, JacobiCtl* ctl, cudaStream_t s) {
     using C = typename CT<T>::type;
     const size_t smem = (size_t)2 * BC * m_max * sizeof(C);
@@ -632,7 +633,9 @@ static cudaError_t launch_bc(const GateDesc* d, int n_gates, int m_max, int n_ma
     long long grid = (long long)sms * per_sm;
     if (grid > visits) grid = visits;
     if (grid < 1) grid = 1;
-    k_jacobi<T, BC, RPL, MINB><<<(unsigned)grid, BC * 32, smem, s>>>(d, n_gates, tol, max_sweeps < 1 ? 1 : max_sweeps, ctl);
+    const int lead = (n_lead < 1 || n_lead > n_gates) ? n_gates : n_lead;
+    k_jacobi<T, BC, RPL, MINB><<<(unsigned)grid, BC * 32, smem, s>>>(d, n_gates, lead, tol,
+                                                                      max_sweeps < 1 ? 1 : max_sweeps, ctl);
     return cudaGetLastError();
 }
 
@@ -644,10 +647,10 @@ static cudaError_t launch_bc(const GateDesc* d, int n_gates, int m_max, int n_ma
 // change this launch.  tnsim_autotune times every configuration on a real layer.
 template <typename T>
 cudaError_t launch_jacobi(const GateDesc* d, int n_gates, int m_max, int n_max, double tol,
-                          int max_sweeps, JacobiCtl* ctl, cudaStream_t s, int cfg) {
+                          int max_sweeps, JacobiCtl* ctl, cudaStream_t s, int cfg, int n_lead) {
     if (n_gates <= 0) return cudaSuccess;
     const bool narrow = (cfg & 1) != 0;
-#define TNSIM_JAC(BC, RPL, MINB) launch_bc<T, BC, RPL, MINB>(d, n_gates, m_max, n_max, tol, max_sweeps, ctl, s)
+#define TNSIM_JAC(BC, RPL, MINB) launch_bc<T, BC, RPL, MINB>(d, n_gates, n_lead, m_max, n_max, tol, max_sweeps, ctl, s)
     if (m_max <= 64) return narrow ? TNSIM_JAC(8, 2, 2) : TNSIM_JAC(16, 2, 1);
     if (m_max <= 128) return narrow ? TNSIM_JAC(8, 4, 2) : TNSIM_JAC(16, 4, 1);
     if (m_max <= 256) return narrow ? TNSIM_JAC(8, 8, 2) : TNSIM_JAC(16, 8, 1);
@@ -661,7 +664,9 @@ cudaError_t launch_jacobi(const GateDesc* d, int n_gates, int m_max, int n_max, 
 #undef TNSIM_JAC
 }
 
-template cudaError_t launch_jacobi<float>(const GateDesc*, int, int, int, double, int, JacobiCtl*, cudaStream_t, int);
-template cudaError_t launch_jacobi<double>(const GateDesc*, int, int, int, double, int, JacobiCtl*, cudaStream_t, int);
+template cudaError_t launch_jacobi<float>(const GateDesc*, int, int, int, double, int, JacobiCtl*, cudaStream_t, int,
+                                          int);
+template cudaError_t launch_jacobi<double>(const GateDesc*, int, int, int, double, int, JacobiCtl*, cudaStream_t, int,
+                                           int);
 
 }  // namespace tnsim

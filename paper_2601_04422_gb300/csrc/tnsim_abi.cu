@@ -119,6 +119,7 @@ struct tnsim_plan {
     bool canon = false;            // some state of the plan is in canonical form
     bool qr = false;               // some state of the plan selected QR preconditioning
     int jac_cfg = 0;               // Jacobi launch configuration of the first state
+    int lead = 0;                  // leading gates of the largest capacity (leading_jobs)
 };
 
 struct tnsim_graph {
@@ -242,6 +243,19 @@ struct GateJob {
     double* eps_dev;           // device or null
 };
 
+// How many leading jobs of a batch sorted by decreasing size share the first job's size
+// (the persistent Jacobi CTAs start spread over them).  cap: compare capacities instead
+// of the current bond bounds (the order frozen plans are sorted in).
+int leading_jobs(const std::vector<GateJob>& jobs, bool cap) {
+    auto key = [cap](const GateJob& j) {
+        const int* b = cap ? j.m->cap.data() : j.m->ub.data();
+        return (double)b[j.q] * b[j.q + 2] * b[j.q + 2];
+    };
+    int k = 0;
+    while (k < (int)jobs.size() && key(jobs[k]) == key(jobs[0])) ++k;
+    return k;
+}
+
 // Fill and upload the descriptors of a batch of gates (possibly from several states).
 // qr_force >= 0 replaces every state's QR-preconditioning choice (the autotuner's descriptors).
 tnsim_status upload_desc(cudaStream_t st, const std::vector<GateJob>& jobs, GateDesc* h_desc,
@@ -326,7 +340,8 @@ tnsim_status launch_gates(cudaStream_t st, const std::vector<GateJob>& jobs, con
         prof_end(pm, st, TNSIM_K_QR, ev);
     }
     ev = prof_begin(pm, st);
-    CUDA_TRY(launch_jacobi<T>(d_desc, ng, m_max, n_max, tol, sweeps, pm->d_ctl, st, pm->jac_cfg));
+    CUDA_TRY(launch_jacobi<T>(d_desc, ng, m_max, n_max, tol, sweeps, pm->d_ctl, st, pm->jac_cfg,
+                              leading_jobs(jobs, false)));
     prof_end(pm, st, TNSIM_K_JACOBI, ev);
     ev = prof_begin(pm, st);
     CUDA_TRY(launch_truncate<T>(d_desc, ng, st));
@@ -946,6 +961,7 @@ tnsim_status tnsim_plan_create(tnsim_mps* const* ms, int32_t n_states, const int
         return ca > cb;
     });
     p->n_gates = (int)jobs.size();
+    p->lead = leading_jobs(jobs, true);
     p->n_s1 = (int)s1.size();
     cudaError_t e = cudaMalloc((void**)&p->d_desc, sizeof(GateDesc) * (p->n_gates + 1));
     if (e == cudaSuccess) e = cudaMalloc((void**)&p->d_out, sizeof(GateOut) * (p->n_gates + 1));
@@ -985,7 +1001,8 @@ tnsim_status tnsim_plan_launch(tnsim_plan* p) {
         CUDA_TRY(launch_theta<double>(p->d_desc, ng, p->chiL_max, p->chiR_max, st));
         if (p->canon) CUDA_TRY(launch_scale_rows<double>(p->d_desc, ng, st));
         if (p->qr) CUDA_TRY(launch_qr<double>(p->d_desc, ng, m_max, st));
-        CUDA_TRY(launch_jacobi<double>(p->d_desc, ng, m_max, n_max, p->tol, p->sweeps, p->d_ctl, st, p->jac_cfg));
+        CUDA_TRY(launch_jacobi<double>(p->d_desc, ng, m_max, n_max, p->tol, p->sweeps, p->d_ctl, st, p->jac_cfg,
+                                       p->lead));
         CUDA_TRY(launch_truncate<double>(p->d_desc, ng, st));
         CUDA_TRY(launch_left<double>(p->d_desc, ng, m_max, p->k_max, st));
         CUDA_TRY(launch_right<double>(p->d_desc, ng, p->k_max, n_max, st));
@@ -997,7 +1014,8 @@ tnsim_status tnsim_plan_launch(tnsim_plan* p) {
         else CUDA_TRY(launch_theta_tc(p->tc_mode, p->d_desc, ng, p->chiL_max, p->chiM_max, p->chiR_max, st));
         if (p->canon) CUDA_TRY(launch_scale_rows<float>(p->d_desc, ng, st));
         if (p->qr) CUDA_TRY(launch_qr<float>(p->d_desc, ng, m_max, st));
-        CUDA_TRY(launch_jacobi<float>(p->d_desc, ng, m_max, n_max, p->tol, p->sweeps, p->d_ctl, st, p->jac_cfg));
+        CUDA_TRY(launch_jacobi<float>(p->d_desc, ng, m_max, n_max, p->tol, p->sweeps, p->d_ctl, st, p->jac_cfg,
+                                      p->lead));
         CUDA_TRY(launch_truncate<float>(p->d_desc, ng, st));
         CUDA_TRY(launch_left<float>(p->d_desc, ng, m_max, p->k_max, st));
         CUDA_TRY(launch_right<float>(p->d_desc, ng, p->k_max, n_max, st));
@@ -1373,6 +1391,7 @@ tnsim_status tnsim_autotune(tnsim_mps* m, int32_t n2, const int32_t* q, const do
     std::memcpy(stg->gates, g4x4, sizeof(double) * 32 * n2);
     CUDA_TRY(cudaMemcpyAsync(m->d_gates, stg->gates, sizeof(double) * 32 * n2, cudaMemcpyHostToDevice, st));
     std::vector<GateJob> jobs = layer_jobs(m, n2, q, m->d_gates, nullptr, nullptr);
+    const int lead = leading_jobs(jobs, false);
     CUDA_TRY(cudaMemsetAsync(m->d_out, 0, sizeof(GateOut) * n2, st));
     s = upload_desc(st, jobs, stg->desc, m->d_desc, nullptr, 1);
     CUDA_TRY(cudaEventRecord(stg->done, st));
@@ -1426,8 +1445,10 @@ tnsim_status tnsim_autotune(tnsim_mps* m, int32_t n2, const int32_t* q, const do
                                        : launch_qr<double>(m->d_desc, n2, m_max, st);
             if (e == cudaSuccess)
                 e = m->dt == TNSIM_C64
-                        ? launch_jacobi<float>(m->d_desc, n2, m_max, n_max, default_tol(m), default_sweeps(m), m->d_ctl, st, c)
-                        : launch_jacobi<double>(m->d_desc, n2, m_max, n_max, default_tol(m), default_sweeps(m), m->d_ctl, st, c);
+                        ? launch_jacobi<float>(m->d_desc, n2, m_max, n_max, default_tol(m), default_sweeps(m), m->d_ctl, st, c,
+                                               lead)
+                        : launch_jacobi<double>(m->d_desc, n2, m_max, n_max, default_tol(m), default_sweeps(m), m->d_ctl, st, c,
+                                                lead);
             if (e == cudaSuccess) e = cudaEventRecord(e1, st);
             if (e == cudaSuccess) e = cudaEventSynchronize(e1);
             float ms = 0.f;

@@ -104,9 +104,11 @@ cudaError_t launch_theta(const GateDesc* d, int n_gates, int chiL_max, int chiR_
 // blocks, 2 CTAs per SM).  The configurations a state can select add QR preconditioning
 // (bit 1 of the state's configuration, GateDesc::qr): kJacobiConfigs of them.
 constexpr int kJacobiConfigs = 4;
+// n_lead: how many leading descriptors (sorted by decreasing size) share the first one's
+// size; the persistent CTAs start spread over them (0: over all gates).
 template <typename T>
 cudaError_t launch_jacobi(const GateDesc* d, int n_gates, int m_max, int n_max, double tol,
-                          int max_sweeps, JacobiCtl* ctl, cudaStream_t s, int cfg = 0);
+                          int max_sweeps, JacobiCtl* ctl, cudaStream_t s, int cfg = 0, int n_lead = 0);
 template <typename T>
 cudaError_t launch_truncate(const GateDesc* d, int n_gates, cudaStream_t s);
 template <typename T>
