@@ -4,14 +4,14 @@
  * The library applies layers of nearest-neighbour two-qubit gates to a Matrix
  * Product State held in GPU memory (HBM).  Per gate on the adjacent pair
  * (q, q+1) it runs the steps of the paper's local two-qubit update (Sec. III.A
- * "Two Qubit Gate", Sec. III.B simulation_kernel, Fig. 2):
+ * "Two Qubit Gate", Sec. IV.A simulation_kernel, Fig. 2):
  *
  *   merge the two sites over their shared bond, contract the 4x4 gate (Eq. 1),
  *   take a truncated SVD of the (2 chi_L) x (2 chi_R) result, write the left
  *   singular vectors into site q and S.V^H into site q+1.
  *
  * All gates of a layer act on disjoint pairs and run in the same launches
- * (Sec. III.B "Parallelizing the TAMM Backend": layers of non-overlapping gates).
+ * (Sec. IV.B "Parallelizing the TAMM Backend": layers of non-overlapping gates).
  *
  * Conventions shared by every entry point
  * ---------------------------------------
@@ -94,7 +94,7 @@ typedef struct {
 tnsim_status tnsim_params_default(tnsim_dtype dt, tnsim_params* out);
 
 /* Create the state |0...0> on n_qubits >= 2 sites with every bond of dimension 1
- * (Sec. III.B "Implementations").  dt selects complex64 (FP32 arithmetic) or
+ * (Sec. IV.A "Implementations").  dt selects complex64 (FP32 arithmetic) or
  * complex128 (FP64 arithmetic).  p may be NULL (defaults).  cuda_stream is a
  * cudaStream_t on which all work of this handle is ordered; NULL makes the
  * library create and own a non-blocking stream.  Device memory for the sites
@@ -107,7 +107,7 @@ tnsim_status tnsim_mps_create(int32_t n_qubits, tnsim_dtype dt, const tnsim_para
 /* Release every device and host resource of m (NULL is accepted). Synchronises m's stream. */
 tnsim_status tnsim_mps_destroy(tnsim_mps* m);
 
-/* Apply one layer (Sec. III.A "One Qubit Gate" / "Two Qubit Gate", Sec. III.B layers):
+/* Apply one layer (Sec. III.A "One Qubit Gate" / "Two Qubit Gate", Sec. IV.B layers):
  *   u1  : NULL, or n_qubits one-qubit gates (8 doubles each) applied to every qubit
  *         BEFORE the two-qubit gates (identity entries are allowed);
  *   q   : n2 left-qubit indices; the pairs (q[i], q[i]+1) must be disjoint;
@@ -128,7 +128,7 @@ tnsim_status tnsim_apply_layer_device(tnsim_mps* m, int32_t n2, const int32_t* q
                                       const double* g4x4_dev, const double* u1_dev,
                                       double* eps_dev);
 
-/* Apply a list of gates on any qubits (Sec. III.B: non-local two-qubit gates by the
+/* Apply a list of gates on any qubits (Sec. IV.B: non-local two-qubit gates by the
  * SWAP method, and layerization into non-overlapping layers).
  *   operation i : qb[i] < 0 -- a one-qubit gate on qubit qa[i], 2x2 in the first 8
  *                 doubles of mats[32*i ...];
@@ -242,7 +242,7 @@ tnsim_status tnsim_amplitudes(tnsim_mps* m, int64_t n_str, const uint8_t* bits,
 tnsim_status tnsim_expect_pauli(tnsim_mps* m, int32_t n_terms, const char* paulis,
                                 double* out);
 
-/* Perfect sampling of n_shots bitstrings (Sec. III.A "Sampling"; Sec. III.B
+/* Perfect sampling of n_shots bitstrings (Sec. III.A "Sampling"; Sec. IV.A
  * measurement).  Qubit by qubit from qubit 0, shot s takes bit b_q = 1 exactly when
  * uniforms[s*n + q] * (p0 + p1) >= p0, where p0, p1 are the weights of the two
  * outcomes given its earlier bits; the prefix is then projected on the outcome

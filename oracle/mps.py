@@ -4,7 +4,7 @@ Test infrastructure only (see the package docstring).  Every site tensor is
 complex128 with shape (chi_q, 2, chi_{q+1}) (Eq. 2: one physical leg, two bond
 legs; the terminal sites have a bond of dimension one).
 
-The two-qubit update follows Sec. III.A "Two Qubit Gate" and Sec. III.B
+The two-qubit update follows Sec. III.A "Two Qubit Gate" and Sec. IV.A
 (``simulation_kernel``) step by step:
 
 1. merge the two sites over their shared bond (Fig. 2, "merge two tensors"):
@@ -13,7 +13,7 @@ The two-qubit update follows Sec. III.A "Two Qubit Gate" and Sec. III.B
    paragraph, first sentence): ``theta[l, a, b, r] = sum_{c,d} G[a, b, c, d] M[l, c, d, r]``;
 3. SVD of theta viewed as the (2 chi_L) x (2 chi_R) matrix with rows (l, a) and
    columns (b, r), with the bond truncated (Sec. II.A best low-rank approximation;
-   Sec. III.B "the bond dimension can be truncated");
+   Sec. IV.A "the bond dimension can be truncated");
 4. the left singular vectors become the left ("control") site and the right
    singular vectors with the singular values contracted in become the right
    ("target") site (Sec. III.A "Two Qubit Gate").
@@ -81,7 +81,7 @@ class MPS:
 
 
 def zero_state(n: int) -> MPS:
-    """|0...0> with every bond of dimension one (Sec. III.B "Implementations")."""
+    """|0...0> with every bond of dimension one (Sec. IV.A "Implementations")."""
     sites = []
     for _ in range(n):
         a = np.zeros((1, 2, 1), dtype=np.complex128)
@@ -217,7 +217,7 @@ def reversed_pair(g: np.ndarray) -> np.ndarray:
 
 def apply_2q_any(mps: MPS, qa: int, qb: int, g: np.ndarray, chi_max: int, cutoff: float = 0.0,
                  renormalize: bool = True, canonical: bool = False) -> List[GateRecord]:
-    """Two-qubit gate on any two distinct qubits by the SWAP method (Sec. III.B
+    """Two-qubit gate on any two distinct qubits by the SWAP method (Sec. IV.B
     simulation_kernel: SWAP gates make the distant sites local, the gate is applied,
     and the SWAPs are reversed).  ``g`` has basis index 2*b_qa + b_qb.
 
@@ -322,7 +322,7 @@ def to_dense(mps: MPS) -> np.ndarray:
 
 
 # --------------------------------------------------------------------------
-# canonical forms and sampling (Sec. III.B "Measurement operations", Sec. III.A "Sampling")
+# canonical forms and sampling (Sec. IV.A "Measurement operations", Sec. III.A "Sampling")
 
 
 def left_canonicalize(mps: MPS) -> MPS:
@@ -350,7 +350,7 @@ def right_canonicalize(mps: MPS) -> MPS:
 
 
 def perfect_sample_u(mps: MPS, u: np.ndarray) -> np.ndarray:
-    """Perfect sampling (Sec. III.A "Sampling"; Sec. III.B: canonicalise, then sample)
+    """Perfect sampling (Sec. III.A "Sampling"; Sec. IV.A: canonicalise, then sample)
     with the random draws given: shot s takes bit b_q = 1 exactly when
     u[s, q] * (p0 + p1) >= p0, where p0, p1 are the weights of the two outcomes of
     qubit q given the bits already drawn.  After each draw the prefix is projected on

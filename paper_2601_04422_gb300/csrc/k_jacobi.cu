@@ -1,6 +1,6 @@
 // Batched one-sided (Hestenes) Jacobi SVD of theta for every gate of a launch.
 //
-// The paper decomposes theta with a Jacobi SVD (cusolverDnZgesvdj, Sec. III.B);
+// The paper decomposes theta with a Jacobi SVD (cusolverDnZgesvdj, Sec. IV.A);
 // here the one-sided variant orthogonalises the n = 2chi_R columns of the
 // m x n column-major working matrix W in place: W <- theta . V with V unitary,
 // so at convergence the columns of W are u_j s_j.  V itself is never formed --

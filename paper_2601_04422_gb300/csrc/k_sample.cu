@@ -1,5 +1,5 @@
 // Perfect sampling of an MPS with memoised prefixes (Sec. III.A "Sampling",
-// Sec. III.B measurement).
+// Sec. IV.A measurement).
 //
 // Shot s draws qubit q from the weights of its two outcomes given its bits so far:
 // with v the (normalised) row vector of its prefix and R_{q+1} the right environment

@@ -5,7 +5,7 @@
 //               them descending (ties: lower column first); the kept rank is
 //                 k = max(1, min(chi_max, #{s_j > eps*max(m,n)*s_max},
 //                                smallest k with sum_{j>=k} s_j^2 <= cutoff*sum s_j^2))
-//               (Sec. II.A: truncate the bond; Sec. III.B: "the bond dimension can be
+//               (Sec. II.A: truncate the bond; Sec. IV.A: "the bond dimension can be
 //               truncated").  The discarded weight and the renormalisation factor
 //               sqrt(sum s^2 / sum_{j<k} s^2) are FP64.  Writes chi[q+1] = k.
 //  k_left     : new left site = left singular vectors (Sec. III.A "Two Qubit Gate"):

@@ -1,5 +1,5 @@
 // Host planner for gate lists: non-local two-qubit gates through SWAP chains, and
-// layerization into layers of disjoint nearest-neighbour pairs (Sec. III.B).
+// layerization into layers of disjoint nearest-neighbour pairs (Sec. IV.B).
 //
 // A two-qubit gate on qubits (a, b) with |a - b| > 1 is made local the way the
 // paper's SWAP method does it: the far qubit b is moved next to a by SWAP gates on

@@ -1,5 +1,5 @@
 // Host planner of gate lists (tnsim_circuit.cu): SWAP chains for non-local gates
-// and as-soon-as-possible layers of disjoint nearest-neighbour pairs (Sec. III.B).
+// and as-soon-as-possible layers of disjoint nearest-neighbour pairs (Sec. IV.B).
 #pragma once
 
 #include <string>

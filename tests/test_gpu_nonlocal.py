@@ -1,4 +1,4 @@
-"""Non-local two-qubit gates through tnsim_apply_circuit (Sec. III.B SWAP method,
+"""Non-local two-qubit gates through tnsim_apply_circuit (Sec. IV.B SWAP method,
 layerization) against the FP64 oracle, which applies the same list in program order.
 
 Gauge-invariant comparisons only (amplitudes, per-bond singular values, discarded

@@ -1,4 +1,4 @@
-"""Non-local two-qubit gates (Sec. III.B SWAP method) and layerization, on the CPU.
+"""Non-local two-qubit gates (Sec. IV.B SWAP method) and layerization, on the CPU.
 
 * the dense any-pair gate (the plain contraction of Eq. 1 on two arbitrary legs)
   against a brute-force sum over basis states and against the closed form of CX;

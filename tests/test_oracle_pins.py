@@ -2,7 +2,7 @@
 
 * brute force: the dense state-vector simulator (full contraction, Eq. 1) at
   <= 10 qubits, where an MPS with an untruncated bond is exact;
-* closed forms: GHZ (Sec. IV.A), the QFT of a basis state (uniform magnitudes
+* closed forms: GHZ (Sec. V.A), the QFT of a basis state (uniform magnitudes
   2^(-n/2) with known phases), product states;
 * invariants: unit norm, left isometries of freshly written left sites,
   canonical forms, sum of s^2 = |theta|_F^2, 1q-only layers keep the bonds;

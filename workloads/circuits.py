@@ -10,7 +10,7 @@ Conventions (fixed once, used everywhere):
 * a two-qubit gate on the adjacent pair (q, q+1) is a 4x4 complex matrix whose
   basis index is ``2*b_q + b_{q+1}`` (row = output, column = input);
 * a one-qubit gate is a 2x2 matrix acting on the physical leg (Eq. 3);
-* a layer is a set of two-qubit gates on disjoint adjacent pairs (Sec. III.B,
+* a layer is a set of two-qubit gates on disjoint adjacent pairs (Sec. IV.B,
   "Parallelizing the TAMM Backend", layerization) plus optional one-qubit
   gates on every qubit that act *before* the two-qubit gates of the layer.
 
