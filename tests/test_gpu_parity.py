@@ -535,18 +535,22 @@ def test_c3_full_size_last_layer(T):
 
 
 @pytest.mark.slow
-def test_full_size_chi256_layer_sampled_gates(T):
+@pytest.mark.parametrize("cfg,gemm", [(0, "FP32"), (2, "TF32X3")])
+def test_full_size_chi256_layer_sampled_gates(T, cfg, gemm):
     """100 qubits, chi_max 256, Haar SU(4) brickwork, complex64, in the batched launch
-    configuration of the benchmark: after the bonds saturate, one more layer is
-    applied on the GPU; for sampled pairs the oracle applies the same gate to the
-    same (exported) input sites and the kept singular values, the discarded weight
-    and the gauge-invariant two-site block A'_q A'_{q+1} are compared."""
+    of the benchmark (configuration 2 with the 3xTF32 contraction is what its
+    autotuner picks; configuration 0 with FP32 is the default): after the bonds
+    saturate, one more layer is applied on the GPU; for sampled pairs the oracle
+    applies the same gate to the same (exported) input sites and the kept singular
+    values, the discarded weight and the gauge-invariant two-site block
+    A'_q A'_{q+1} are compared."""
     n, chi = 100, 256
     circ = W.brickwork_su4(n, 12, seed=7)
-    m = T.MPS(n, dtype=T.TNSIM_C64, chi_max=chi)
+    m = T.MPS(n, dtype=T.TNSIM_C64, chi_max=chi, gemm=getattr(T, "TNSIM_GEMM_" + gemm))
     for lay in circ.layers[:11]:
         m.apply_layer(lay)
     assert int(np.max(m.bond_dims())) == chi
+    T.tnsim_set_jacobi_config(m.h, cfg)
     before = m.export_sites()
     last = circ.layers[11]
     eps = m.apply_layer(last)
