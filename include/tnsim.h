@@ -47,7 +47,7 @@ typedef enum {
     TNSIM_ENOMEM = 2,      /* a device or pinned allocation failed */
     TNSIM_ECUDA = 3,       /* a CUDA runtime call failed (message has the CUDA error) */
     TNSIM_ENOCONV = 4,     /* a Jacobi SVD reached max_sweeps; the layer was still applied */
-    TNSIM_ETIMEOUT = 5,    /* reserved: a bounded device wait ran out */
+    TNSIM_ETIMEOUT = 5,    /* a bounded device wait ran out; the layer is incomplete (state undefined) */
     TNSIM_EUNSUPPORTED = 6 /* entry point or mode not available in this build */
 } tnsim_status;
 
@@ -82,7 +82,8 @@ typedef struct {
     double cutoff;      /* relative discarded-weight cutoff in [0, 1); 0 = none */
     int32_t renormalize;/* 1: rescale kept singular values so sum s^2 is unchanged */
     int32_t max_sweeps; /* Jacobi sweep cap; 0 = default (40 c64, 60 c128) */
-    double jacobi_tol;  /* rotate a column pair while |g| > tol*sqrt(a*b); 0 = default */
+    double jacobi_tol;  /* rotate a column pair while |g| > tol*sqrt(a*b); 0 = default
+                           (complex64: 2 eps_32; complex128: max(sqrt(2 chi_L), 4) eps_64) */
     int32_t schedule;   /* tnsim_schedule */
     int32_t gemm;       /* tnsim_gemm_mode (complex64 only) */
     int32_t form;       /* tnsim_form */
@@ -115,7 +116,8 @@ tnsim_status tnsim_mps_destroy(tnsim_mps* m);
  * eps_out (may be NULL) receives the relative discarded weight of each gate,
  * sum_{j>=k} s_j^2 / sum_j s_j^2.  The call is synchronous: it returns after the
  * layer finished on the GPU.  Errors: EINVAL (bad pair list, non-finite gate,
- * n2 < 0; nothing launched), ENOCONV (layer applied, an SVD hit max_sweeps), ECUDA. */
+ * n2 < 0; nothing launched), ENOCONV (layer applied, an SVD hit max_sweeps),
+ * ETIMEOUT (a bounded device wait ran out, see tnsim_set_wait_limits), ECUDA. */
 tnsim_status tnsim_apply_layer(tnsim_mps* m, int32_t n2, const int32_t* q,
                                const double* g4x4, const double* u1, double* eps_out);
 
@@ -274,6 +276,33 @@ tnsim_status tnsim_sample(tnsim_mps* m, int64_t n_shots, const double* uniforms,
  * launches of m.  Errors: EINVAL. */
 tnsim_status tnsim_set_jacobi_config(tnsim_mps* m, int32_t cfg);
 
+/* Limits of the two bounded waits inside the layer kernels (no kernel traps or waits
+ * forever; a wait that runs out is reported through the gate's status word).  The paper
+ * has no counterpart: it is the failure handling of this library's persistent launch.
+ *   jacobi_idle_polls : polls (each followed by a short sleep) an idle CTA of the
+ *                       persistent Jacobi launch makes without seeing any gate's round
+ *                       complete before it sets the launch's error flag; every CTA then
+ *                       leaves, the unfinished gates report status 5;
+ *   mbarrier_polls    : polls of one mbarrier wait (TMA copies landed, MMAs done) in the
+ *                       tensor-core contraction; on timeout the CTA waits (with the default
+ *                       limit) for the copies or MMAs it already issued, then leaves and
+ *                       reports status 5 for its gate.
+ * 0 restores a default (2^22 and 2^26 polls: about a second or more, far beyond any
+ * legitimate wait).
+ * Calls after a timeout return ETIMEOUT; the state is undefined but the handle and
+ * the CUDA context stay usable (import sites or start again).
+ * Errors: EINVAL (NULL state, negative limit or one beyond 32 bits). */
+tnsim_status tnsim_set_wait_limits(tnsim_mps* m, int64_t jacobi_idle_polls, int64_t mbarrier_polls);
+
+/* Process-wide cap on the device memory held by the states of this library (0 = no cap,
+ * the default).  tnsim_mps_create computes every device allocation of the new state
+ * before making any, and returns ENOMEM, allocating nothing, when the bytes already held
+ * plus the new state's would exceed the cap.  Errors: EINVAL (negative bytes). */
+tnsim_status tnsim_set_device_memory_cap(int64_t bytes);
+
+/* Device bytes held by the live states of this process (as counted for the cap). */
+int64_t tnsim_device_bytes_held(void);
+
 /* Autotuner of the Jacobi SVD: contract the given layer (n2 >= 1 pairs q, gates
  * g4x4 on the host, as in tnsim_apply_layer) of the current state into the work
  * space, then time the persistent Jacobi launch of that layer in every
@@ -380,13 +409,14 @@ tnsim_status tnsim_profile_read(tnsim_mps* m, double* ms, int64_t* launches);
  *   cuda_stream : the cudaStream_t to run on (NULL = the legacy default stream);
  *   k_out   : host, the kept bond dimension; eps_out (host, may be NULL) the
  *             discarded weight; s_out (host, may be NULL, chi_max doubles) the kept
- *             singular values.
+ *             singular values in its first k entries (the rest set to 0).
  * Limits: chi_l, chi_r <= 128 and chi_max <= 256 (EINVAL beyond).  Scratch is one
  * fixed array of about 1.1 MB compiled into the library, held by every GPU that
  * loads it until the process exits.  The first call on a device looks up that
  * array's device address; make that first call before any stream capture.  All
  * calls share the array, so calls whose work overlaps on the GPU race.  Synchronous.
- * Errors: EINVAL, ENOCONV (the update was applied), ECUDA, EUNSUPPORTED. */
+ * Errors: EINVAL, ENOCONV (the update was applied), ETIMEOUT (the Jacobi kernel gave up
+ * waiting; the sites are undefined), ECUDA, EUNSUPPORTED. */
 tnsim_status tnsim_two_site_update_noalloc(void* site_a, int64_t cap_a, void* site_b,
                                            int64_t cap_b, int32_t chi_l, int32_t chi_m,
                                            int32_t chi_r, const double* g4x4, int32_t chi_max,

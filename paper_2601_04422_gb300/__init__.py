@@ -17,5 +17,6 @@ from ._abi import (  # noqa: F401
     tnsim_two_site_update_noalloc, tnsim_plan_create, tnsim_plan_launch, tnsim_plan_destroy,
     tnsim_graph_create, tnsim_graph_launch, tnsim_graph_destroy, tnsim_apply_circuit,
     tnsim_circuit_layerize, tnsim_sample, tnsim_set_jacobi_config, tnsim_autotune, TNSIM_JACOBI_CONFIGS,
+    tnsim_set_wait_limits, tnsim_set_device_memory_cap, tnsim_device_bytes_held,
     MPS,
 )

@@ -112,6 +112,9 @@ _sig("tnsim_circuit_layerize", C.c_int, [C.c_int32, C.c_int32, _I32P, _I32P, _DP
                                          _I32P, _I32P, _I32P, _I32P, _DP, _DP])
 _sig("tnsim_sample", C.c_int, [_P, C.c_int64, _DP, C.POINTER(C.c_uint8), _I64P])
 _sig("tnsim_set_jacobi_config", C.c_int, [_P, C.c_int32])
+_sig("tnsim_set_wait_limits", C.c_int, [_P, C.c_int64, C.c_int64])
+_sig("tnsim_set_device_memory_cap", C.c_int, [C.c_int64])
+_sig("tnsim_device_bytes_held", C.c_int64, [])
 _sig("tnsim_autotune", C.c_int, [_P, C.c_int32, _I32P, _DP, C.c_int32, _I32P, _DP])
 _sig("tnsim_last_error", C.c_char_p, [])
 _sig("tnsim_version", C.c_char_p, [])
@@ -126,7 +129,7 @@ def exported_symbols():
             "tnsim_profile_enable", "tnsim_profile_read", "tnsim_two_site_update_noalloc",
             "tnsim_plan_create", "tnsim_plan_launch", "tnsim_plan_destroy", "tnsim_graph_create",
             "tnsim_graph_launch", "tnsim_graph_destroy", "tnsim_apply_circuit", "tnsim_circuit_layerize", "tnsim_sample", "tnsim_set_jacobi_config",
-            "tnsim_autotune",
+            "tnsim_autotune", "tnsim_set_wait_limits", "tnsim_set_device_memory_cap", "tnsim_device_bytes_held",
             "tnsim_last_error", "tnsim_version"]
 
 
@@ -344,6 +347,20 @@ TNSIM_JACOBI_CONFIGS = 4
 
 def tnsim_set_jacobi_config(h, cfg: int):
     _check(lib.tnsim_set_jacobi_config(h, int(cfg)))
+
+
+def tnsim_set_wait_limits(h, jacobi_idle_polls: int = 0, mbarrier_polls: int = 0):
+    """Poll limits of the bounded device waits (0 = defaults)."""
+    _check(lib.tnsim_set_wait_limits(h, int(jacobi_idle_polls), int(mbarrier_polls)))
+
+
+def tnsim_set_device_memory_cap(nbytes: int):
+    """Process-wide cap on the device bytes held by states (0 = none)."""
+    _check(lib.tnsim_set_device_memory_cap(int(nbytes)))
+
+
+def tnsim_device_bytes_held() -> int:
+    return int(lib.tnsim_device_bytes_held())
 
 
 def tnsim_autotune(h, q, g4x4, reps: int = 3):

@@ -266,14 +266,18 @@ __global__ void __launch_bounds__(256) k_gate_bwd(const GradGateDesc* __restrict
     }
     if (need_disc) {
         const int dd = nz - k;
-        // Lorentzian broadening of the cut's denominators, eps s_max^4 (at a degenerate cut
-        // the truncated map is not differentiable; this keeps the result finite)
-        const double sk0 = d.s2[0];
-        const double eps_b = EpsG<T>::v * sk0 * sk0;
+        // Lorentzian broadening of the cut's denominators on the scale of their rounding
+        // error: s_j^2 - s_l^2 carries an absolute error ~ eps s_max (s_j + s_l), so the
+        // broadening is (eps s_max (s_j + s_l))^2 -- it regularises unresolved (degenerate)
+        // pairs, where the truncated map is not differentiable, and leaves small but
+        // separated singular values alone
+        const double e2s = EpsG<T>::v * EpsG<T>::v * d.s2[0];
         // X1 = G o B_D (dd x k), B_D = rows k.. of Q1
         for (int i = tid; i < dd * k; i += nt) {
             const int l = i / k, j = i % k;
             const double dj = d.s2[j] - d.s2[k + l];
+            const double sum = sqrt(d.s2[j]) + sqrt(fmax(d.s2[k + l], 0.0));
+            const double eps_b = e2s * sum * sum;
             const T g = d.s2[j] > tau2s ? (T)(dj / (dj * dj + eps_b)) : (T)0;
             C b = Q1[(size_t)(k + l) * k + j];
             b.x *= g;

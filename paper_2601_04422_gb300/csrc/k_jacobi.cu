@@ -28,8 +28,11 @@
 // any gate from a device-side queue, so gates of different sizes and all rounds of
 // a layer share the machine without waves.  The visits of a round are independent;
 // a gate's next round opens when the last visit of the current one is reported.  An
-// idle CTA polls with a sleep; if nothing progresses for ~2^22 polls it sets an
-// error flag and leaves (the host reports ETIMEOUT).  No other wait exists.
+// idle CTA polls with a sleep; if nothing progresses for spin_limit polls (default
+// 2^22, settable per state) it sets an error flag and leaves; every other CTA leaves
+// at its next claim, abandoning the claim, and the unfinished gates report status 5
+// (the host reports ETIMEOUT).  No other wait exists, and no CTA leaves with a copy
+// in flight.
 #include <float.h>
 
 #include "tnsim_internal.h"
@@ -341,7 +344,7 @@ __device__ __forceinline__ Tour tour_of(const GateDesc& d) {
     return t;
 }
 
-constexpr unsigned kSpinLimit = 1u << 22;   // idle polls without any progress before giving up
+constexpr unsigned kSpinLimit = 1u << 22;   // default idle polls without any progress before giving up
 constexpr int kScanTable = 2048;              // gates whose visit count is cached in shared memory
 
 // Warp-parallel claim of one visit (warp 0): each lane checks one gate per pass (one
@@ -402,7 +405,7 @@ __device__ __forceinline__ void claim_scan(const GateDesc* __restrict__ gd, int 
 template <typename T, int BC, int RPL, int MINB>
 __global__ void __launch_bounds__(BC * 32, MINB)
 k_jacobi(const GateDesc* __restrict__ gd, int n_gates, int n_lead, double tol_in, int max_sweeps,
-         JacobiCtl* __restrict__ ctl) {
+         JacobiCtl* __restrict__ ctl, unsigned spin_limit) {
     using C = typename CT<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* X = reinterpret_cast<C*>(smem_raw);       // [2*BC][m], column-major
@@ -422,16 +425,19 @@ k_jacobi(const GateDesc* __restrict__ gd, int n_gates, int n_lead, double tol_in
     __syncthreads();
 
     int have_next = 0, nxt_g = -1, nxt_rnd = 0, nxt_v = 0;   // warp 0: a claim made during the last visit
+    int nxt_err = 0;                                          // the error flag read during the last visit
     for (;;) {
         if (warp == 0) {
-            int found = 0, fg = -1, frnd = 0, fv = 0;
+            int found = 0, fg = -1, frnd = 0, fv = 0, err = 0;
             if (have_next) {
                 found = 1;
                 fg = nxt_g;
                 frnd = nxt_rnd;
                 fv = nxt_v;
+                err = nxt_err;
                 have_next = 0;
             } else {
+                if (lane == 0) err = *((volatile int*)&ctl->error);
                 claim_scan<BC>(gd, n_gates, s_V, scan0, lane, found, fg, frnd, fv);
             }
             if (found) scan0 = fg;
@@ -440,8 +446,10 @@ k_jacobi(const GateDesc* __restrict__ gd, int n_gates, int n_lead, double tol_in
                 s_g = found ? fg : -1;
                 s_rnd = frnd;
                 s_v = fv;
-                if (!found && (*((volatile int*)&ctl->n_finished) >= n_gates ||
-                               *((volatile int*)&ctl->error)))
+                // after a timeout every CTA leaves, a claim in hand included: the gates
+                // left unfinished report status 5
+                if (err || (!found && (*((volatile int*)&ctl->n_finished) >= n_gates ||
+                                       *((volatile int*)&ctl->error))))
                     s_exit = 1;
                 s_rot = 0;
                 s_vis = 0;
@@ -455,7 +463,7 @@ k_jacobi(const GateDesc* __restrict__ gd, int n_gates, int n_lead, double tol_in
                 if (p != last_progress) {
                     last_progress = p;
                     spins = 0;
-                } else if (++spins > kSpinLimit) {
+                } else if (++spins > spin_limit) {
                     atomicExch(&ctl->error, 1);
                 }
                 __nanosleep(256);
@@ -472,9 +480,15 @@ k_jacobi(const GateDesc* __restrict__ gd, int n_gates, int n_lead, double tol_in
         const int m = tg.m, n = tg.n, nb = tg.nb, P = tg.P, R = tg.R;
         const int sweep = rnd / R, round = rnd - sweep * R;
         C* Wm = (C*)d.W;
-        // default tolerance sqrt(m) * eps (LAPACK's one-sided Jacobi uses the same scale),
-        // floored at 4 eps for tiny m; a column below eps*sqrt(max(m,n))*|theta|_F is zero
-        const double tol = tol_in > 0.0 ? tol_in : fmax(sqrt((double)m), 4.0) * Eps<T>::v;
+        // default tolerance: FP64, sqrt(m) * eps (LAPACK's one-sided Jacobi uses the same
+        // scale), floored at 4 eps for tiny m; FP32, 2 eps.  Near convergence the columns
+        // are almost orthogonal, so the FP32 partial sums of g stay small and its rounding
+        // error is a fraction of eps sqrt(a b): the tighter test is resolvable, and it
+        // matters because a pair left non-orthogonal at tol tilts the kept subspace by
+        // about tol / (relative gap at the cut).  A column below eps*sqrt(max(m,n))*|theta|_F
+        // is zero.
+        const double tol = tol_in > 0.0 ? tol_in
+                                        : (sizeof(T) == 4 ? 2.0 * Eps<T>::v : fmax(sqrt((double)m), 4.0) * Eps<T>::v);
         const T tol2 = (T)(tol * tol);
         const T zthr = (T)(Eps<T>::v * Eps<T>::v * (double)max(m, n) * out->frob2);
 
@@ -568,6 +582,7 @@ k_jacobi(const GateDesc* __restrict__ gd, int n_gates, int n_lead, double tol_in
         // never waits while holding a claim, so claiming before this visit's report is safe)
         if (warp == 0) {
             int found, fg, frnd, fv;
+            if (lane == 0) nxt_err = *((volatile int*)&ctl->error);
             claim_scan<BC>(gd, n_gates, s_V, scan0, lane, found, fg, frnd, fv);
             have_next = found;
             nxt_g = fg;
@@ -595,7 +610,8 @@ k_jacobi(const GateDesc* __restrict__ gd, int n_gates, int n_lead, double tol_in
                     if (rs == 0 || sweep + 1 >= max_sweeps) {
                         fin = true;
                         out->sweeps = sweep + 1;
-                        out->status = (rs == 0) ? 0 : 4;
+                        // keep a timeout the contraction reported (5) before this launch
+                        if (rs != 0 && out->status < 4) out->status = 4;
                     }
                 }
                 __threadfence();
@@ -614,7 +630,7 @@ k_jacobi(const GateDesc* __restrict__ gd, int n_gates, int n_lead, double tol_in
 
 template <typename T, int BC, int RPL, int MINB>
 static cudaError_t launch_bc(const GateDesc* d, int n_gates, int n_lead, int m_max, int n_max, double tol,
-                             int max_sweeps, JacobiCtl* ctl, cudaStream_t s) {
+                             int max_sweeps, JacobiCtl* ctl, cudaStream_t s, unsigned spin_limit) {
     using C = typename CT<T>::type;
     const size_t smem = (size_t)2 * BC * m_max * sizeof(C);
     cudaError_t e = cudaFuncSetAttribute(k_jacobi<T, BC, RPL, MINB>,
@@ -635,7 +651,8 @@ static cudaError_t launch_bc(const GateDesc* d, int n_gates, int n_lead, int m_m
     if (grid < 1) grid = 1;
     const int lead = (n_lead < 1 || n_lead > n_gates) ? n_gates : n_lead;
     k_jacobi<T, BC, RPL, MINB><<<(unsigned)grid, BC * 32, smem, s>>>(d, n_gates, lead, tol,
-                                                                      max_sweeps < 1 ? 1 : max_sweeps, ctl);
+                                                                      max_sweeps < 1 ? 1 : max_sweeps, ctl,
+                                                                      spin_limit ? spin_limit : kSpinLimit);
     return cudaGetLastError();
 }
 
@@ -647,10 +664,11 @@ static cudaError_t launch_bc(const GateDesc* d, int n_gates, int n_lead, int m_m
 // change this launch.  tnsim_autotune times every configuration on a real layer.
 template <typename T>
 cudaError_t launch_jacobi(const GateDesc* d, int n_gates, int m_max, int n_max, double tol,
-                          int max_sweeps, JacobiCtl* ctl, cudaStream_t s, int cfg, int n_lead) {
+                          int max_sweeps, JacobiCtl* ctl, cudaStream_t s, int cfg, int n_lead,
+                          unsigned spin_limit) {
     if (n_gates <= 0) return cudaSuccess;
     const bool narrow = (cfg & 1) != 0;
-#define TNSIM_JAC(BC, RPL, MINB) launch_bc<T, BC, RPL, MINB>(d, n_gates, n_lead, m_max, n_max, tol, max_sweeps, ctl, s)
+#define TNSIM_JAC(BC, RPL, MINB) launch_bc<T, BC, RPL, MINB>(d, n_gates, n_lead, m_max, n_max, tol, max_sweeps, ctl, s, spin_limit)
     if (m_max <= 64) return narrow ? TNSIM_JAC(8, 2, 2) : TNSIM_JAC(16, 2, 1);
     if (m_max <= 128) return narrow ? TNSIM_JAC(8, 4, 2) : TNSIM_JAC(16, 4, 1);
     if (m_max <= 256) return narrow ? TNSIM_JAC(8, 8, 2) : TNSIM_JAC(16, 8, 1);
@@ -665,8 +683,8 @@ cudaError_t launch_jacobi(const GateDesc* d, int n_gates, int m_max, int n_max, 
 }
 
 template cudaError_t launch_jacobi<float>(const GateDesc*, int, int, int, double, int, JacobiCtl*, cudaStream_t, int,
-                                          int);
+                                          int, unsigned);
 template cudaError_t launch_jacobi<double>(const GateDesc*, int, int, int, double, int, JacobiCtl*, cudaStream_t, int,
-                                           int);
+                                           int, unsigned);
 
 }  // namespace tnsim

@@ -20,8 +20,11 @@
 //      tcgen05.ld (thread = row), exchanges the partner row (l, 1 - p0) by shuffle,
 //      applies the 4x4 gate in registers and writes theta column-major into W and
 //      theta0, accumulating |theta|_F^2 in FP64.
-// Every wait on an mbarrier is bounded; on timeout the gate's status is set to 5
-// (reported as ETIMEOUT) and the CTA releases its TMEM and returns.
+// Every wait on an mbarrier is bounded (GateDesc::wait_polls polls, default 2^26).  On
+// timeout the CTA stops issuing work, waits (again bounded, with the default limit)
+// for the one barrier phase still pending -- the TMA copies or the MMAs it issued --
+// so that nothing it started still writes its shared memory or its TMEM, then sets
+// the gate's status to 5 (reported as ETIMEOUT), releases its TMEM and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
@@ -34,7 +37,7 @@ constexpr int TC_M = 128;          // output tile rows (64 l x 2 p0)
 constexpr int TC_RH = 64;          // r values per tile (two halves: p1 = 0, 1)
 constexpr int TC_N = 2 * TC_RH;    // output tile columns
 constexpr int TC_THREADS = 128;
-constexpr unsigned kTcSpin = 1u << 24;
+constexpr unsigned kTcSpin = 1u << 26;     // default polls of a bounded mbarrier wait (about a second)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -130,11 +133,13 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
-    for (unsigned i = 0; i < kTcSpin; ++i) {
+// One poll is one non-blocking test of the phase (mbarrier.test_wait), so a limit
+// counts checks, not an implementation-defined suspend time.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase, unsigned limit) {
+    for (unsigned i = 0; i < limit; ++i) {
         uint32_t done;
         asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
             " selp.u32 %0, 1, 0, p;\n}\n"
             : "=r"(done)
             : "r"(bar), "r"(phase)
@@ -260,6 +265,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_theta_tc(const GateDesc* __re
     const int zA = d.tc_slot * 8, zB = d.tc_slot * 8 + 4;
     const uint32_t sbase = smem_u32(tiles);
     const int nk = kuse / KS;
+    const unsigned lim = d.wait_polls > 0 ? (unsigned)d.wait_polls : kTcSpin;
+    uint32_t pend_bar = 0, pend_phase = 0;   // the barrier phase left pending by a timeout
     for (int kb = 0; kb < nk; ++kb) {
         if (tid == 0 && !s_fail) {
             mbar_expect_tx(smem_u32(&bar_full), 8 * TILE);
@@ -269,9 +276,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_theta_tc(const GateDesc* __re
                 tma_load_3d(sbase + (4 + p) * TILE + TILE / 2, mapB, kb * KS, chiR + r0, zB + p, smem_u32(&bar_full));
             }
         }
-        if (!mbar_wait(smem_u32(&bar_full), kb & 1)) { if (lane == 0) atomicExch(&s_fail, 1); }
+        if (!mbar_wait(smem_u32(&bar_full), kb & 1, lim)) atomicExch(&s_fail, 1);
         __syncthreads();
-        if (s_fail) break;
+        if (s_fail) {
+            // the copies of this stage may still be in flight (no MMA of it was issued)
+            pend_bar = smem_u32(&bar_full);
+            pend_phase = kb & 1;
+            break;
+        }
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             // plane tiles: 0 A_re_hi, 1 A_re_lo, 2 A_im_hi, 3 A_im_lo, 4 B_re_hi, 5 B_re_lo, 6 B_im_hi, 7 B_im_lo
@@ -304,10 +316,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_theta_tc(const GateDesc* __re
                          : "memory");
         }
         // the stage buffers are reused by the next TMA only after the MMAs read them
-        if (!mbar_wait(smem_u32(&bar_mma), kb & 1)) { if (lane == 0) atomicExch(&s_fail, 1); }
+        if (!mbar_wait(smem_u32(&bar_mma), kb & 1, lim)) atomicExch(&s_fail, 1);
         __syncthreads();
-        if (s_fail) break;
+        if (s_fail) {
+            // this stage's copies have landed; its MMAs may still be running
+            pend_bar = smem_u32(&bar_mma);
+            pend_phase = kb & 1;
+            break;
+        }
     }
+    if (s_fail && tid == 0) mbar_wait(pend_bar, pend_phase, kTcSpin);   // drain before TMEM and smem go
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
     if (!s_fail) {

@@ -12,6 +12,7 @@
 // The host keeps upper bounds ub_b >= chi_b to size grids; the kernels exit early
 // outside the live dimensions.  Synchronising calls refresh ub from chi.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -44,6 +45,10 @@ tnsim_status fail(tnsim_status s, const std::string& msg) {
     } while (0)
 
 constexpr int kRing = 4;           // pinned staging slots per state
+
+// Process-wide cap on the device memory that states hold (0 = none) and the bytes held.
+std::atomic<int64_t> g_dev_cap{0};
+std::atomic<int64_t> g_dev_held{0};
 constexpr int kMaxChi = 512;       // largest supported chi_max
 
 struct Staging {
@@ -86,6 +91,9 @@ struct tnsim_mps {
     unsigned long long* d_stats = nullptr;   // the counters of tnsim_stats
     JacobiCtl* d_ctl = nullptr;    // control word of the persistent Jacobi launch
     int jac_cfg = 0;               // Jacobi launch configuration (tnsim_set_jacobi_config / tnsim_autotune)
+    unsigned jac_spin = 0;         // idle polls of the Jacobi kernel before it gives up (0 = default)
+    int tc_spin = 0;               // polls of a tensor-core mbarrier wait before it gives up (0 = default)
+    int64_t dev_bytes = 0;         // device bytes held, counted against the process-wide cap
     // tensor-core contraction (complex64 with gemm TF32X3 / BF16X3)
     int tc_mode = -1;              // -1 none, 0 TF32 planes, 1 BF16 planes
     void* d_planes = nullptr;      // [G * 8][tc_rows][tc_k] plane buffer
@@ -119,6 +127,7 @@ struct tnsim_plan {
     bool canon = false;            // some state of the plan is in canonical form
     bool qr = false;               // some state of the plan selected QR preconditioning
     int jac_cfg = 0;               // Jacobi launch configuration of the first state
+    unsigned jac_spin = 0;         // idle-poll limit of the first state
     int lead = 0;                  // leading gates of the largest capacity (leading_jobs)
 };
 
@@ -168,6 +177,8 @@ void free_all(tnsim_mps* m) {
     m->ev_pool.clear();
     m->recs.clear();
     if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);
+    g_dev_held.fetch_sub(m->dev_bytes);
+    m->dev_bytes = 0;
 }
 
 cudaEvent_t prof_event(tnsim_mps* m) {
@@ -299,6 +310,7 @@ tnsim_status upload_desc(cudaStream_t st, const std::vector<GateJob>& jobs, Gate
         d.lam = m->d_spec + (size_t)j.q * m->p.chi_max;
         d.lam_k = m->d_spec_k + j.q;
         d.qr = qr_force >= 0 ? qr_force : (m->jac_cfg >> 1) & 1;
+        d.wait_polls = m->tc_spin;
     }
     CUDA_TRY(cudaMemcpyAsync(d_desc, h_desc, sizeof(GateDesc) * ng, cudaMemcpyHostToDevice, st));
     return TNSIM_OK;
@@ -341,7 +353,7 @@ tnsim_status launch_gates(cudaStream_t st, const std::vector<GateJob>& jobs, con
     }
     ev = prof_begin(pm, st);
     CUDA_TRY(launch_jacobi<T>(d_desc, ng, m_max, n_max, tol, sweeps, pm->d_ctl, st, pm->jac_cfg,
-                              leading_jobs(jobs, false)));
+                              leading_jobs(jobs, false), pm->jac_spin));
     prof_end(pm, st, TNSIM_K_JACOBI, ev);
     ev = prof_begin(pm, st);
     CUDA_TRY(launch_truncate<T>(d_desc, ng, st));
@@ -538,6 +550,28 @@ tnsim_status tnsim_mps_create(int32_t n_qubits, tnsim_dtype dt, const tnsim_para
     } while (0)
 
     m->arena_bytes = off;
+    // every device allocation of the state, checked against the process-wide cap first
+    const bool use_tc = dt == TNSIM_C64 && (prm.gemm == TNSIM_GEMM_TF32X3 || prm.gemm == TNSIM_GEMM_BF16X3);
+    {
+        const size_t capmax2 = (size_t)(2 * m->capmax);
+        int64_t need = (int64_t)(off + sizeof(int) * (n_qubits + 1) + nG * 2 * m->ws_elems * m->esz +
+                                 nG * capmax2 * (sizeof(double) + sizeof(int)) +
+                                 (size_t)(n_qubits + 1) * prm.chi_max * sizeof(double) + sizeof(int) * (n_qubits + 1) +
+                                 nG * (sizeof(GateOut) + sizeof(GateDesc)) + (size_t)n_qubits * sizeof(Site1Desc) +
+                                 gate_doubles * sizeof(double) + sizeof(int) + sizeof(tnsim_stats) + sizeof(JacobiCtl));
+        if (use_tc) need += (int64_t)(nG * 8 * capmax2 * ((m->capmax + 63) / 64 * 64) * sizeof(float) +
+                                      2 * sizeof(CUtensorMap));
+        const int64_t cap = g_dev_cap.load();
+        const int64_t held = g_dev_held.fetch_add(need) + need;
+        if (cap > 0 && held > cap) {
+            g_dev_held.fetch_sub(need);
+            delete m;
+            return fail(TNSIM_ENOMEM, "the state needs " + std::to_string(need) + " device bytes; with " +
+                                          std::to_string(held - need) + " held, that exceeds the cap of " +
+                                          std::to_string(cap) + " bytes (tnsim_set_device_memory_cap)");
+        }
+        m->dev_bytes = need;
+    }
     ALLOC(m->d_sites, off);
     ALLOC(m->d_chi, sizeof(int) * (n_qubits + 1));
     ALLOC(m->d_ws, nG * 2 * m->ws_elems * m->esz);
@@ -563,7 +597,7 @@ tnsim_status tnsim_mps_create(int32_t n_qubits, tnsim_dtype dt, const tnsim_para
             return fail(TNSIM_ECUDA, "cudaEventCreate failed");
         }
     }
-    if (dt == TNSIM_C64 && (prm.gemm == TNSIM_GEMM_TF32X3 || prm.gemm == TNSIM_GEMM_BF16X3)) {
+    if (use_tc) {
         m->tc_mode = prm.gemm == TNSIM_GEMM_TF32X3 ? 0 : 1;
         m->tc_rows = 2 * m->capmax;
         m->tc_k = (m->capmax + 63) / 64 * 64;
@@ -604,6 +638,8 @@ tnsim_status tnsim_mps_create(int32_t n_qubits, tnsim_dtype dt, const tnsim_para
     if (e == cudaSuccess) e = cudaMemset(m->d_sticky, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(m->d_stats, 0, sizeof(tnsim_stats));
     if (e == cudaSuccess) e = cudaMemset(m->d_out, 0, nG * sizeof(GateOut));
+    // finite contents from the start: a contraction that timed out leaves its W unwritten
+    if (e == cudaSuccess) e = cudaMemset(m->d_ws, 0, nG * 2 * m->ws_elems * m->esz);
     if (e != cudaSuccess) {
         free_all(m); delete m;
         return fail(TNSIM_ECUDA, std::string("initialisation: ") + cudaGetErrorString(e));
@@ -914,6 +950,7 @@ tnsim_status tnsim_plan_create(tnsim_mps* const* ms, int32_t n_states, const int
     p->gemm = m0->p.gemm;
     for (int i = 0; i < n_states; ++i) p->canon = p->canon || ms[i]->p.form == TNSIM_FORM_CANONICAL;
     p->jac_cfg = m0->jac_cfg;
+    p->jac_spin = m0->jac_spin;
     for (int i = 0; i < n_states; ++i) p->qr = p->qr || (ms[i]->jac_cfg & 2) != 0;
     p->tc_mode = m0->tc_mode;
     p->tol = m0->p.jacobi_tol;
@@ -1002,7 +1039,7 @@ tnsim_status tnsim_plan_launch(tnsim_plan* p) {
         if (p->canon) CUDA_TRY(launch_scale_rows<double>(p->d_desc, ng, st));
         if (p->qr) CUDA_TRY(launch_qr<double>(p->d_desc, ng, m_max, st));
         CUDA_TRY(launch_jacobi<double>(p->d_desc, ng, m_max, n_max, p->tol, p->sweeps, p->d_ctl, st, p->jac_cfg,
-                                       p->lead));
+                                       p->lead, p->jac_spin));
         CUDA_TRY(launch_truncate<double>(p->d_desc, ng, st));
         CUDA_TRY(launch_left<double>(p->d_desc, ng, m_max, p->k_max, st));
         CUDA_TRY(launch_right<double>(p->d_desc, ng, p->k_max, n_max, st));
@@ -1015,7 +1052,7 @@ tnsim_status tnsim_plan_launch(tnsim_plan* p) {
         if (p->canon) CUDA_TRY(launch_scale_rows<float>(p->d_desc, ng, st));
         if (p->qr) CUDA_TRY(launch_qr<float>(p->d_desc, ng, m_max, st));
         CUDA_TRY(launch_jacobi<float>(p->d_desc, ng, m_max, n_max, p->tol, p->sweeps, p->d_ctl, st, p->jac_cfg,
-                                      p->lead));
+                                      p->lead, p->jac_spin));
         CUDA_TRY(launch_truncate<float>(p->d_desc, ng, st));
         CUDA_TRY(launch_left<float>(p->d_desc, ng, m_max, p->k_max, st));
         CUDA_TRY(launch_right<float>(p->d_desc, ng, p->k_max, n_max, st));
@@ -1367,6 +1404,24 @@ tnsim_status tnsim_sample(tnsim_mps* m, int64_t n_shots, const double* uniforms,
     if (n_nodes_out) *n_nodes_out = (int64_t)c1.total - c1.nodes;
     return TNSIM_OK;
 }
+
+tnsim_status tnsim_set_wait_limits(tnsim_mps* m, int64_t jacobi_idle_polls, int64_t mbarrier_polls) {
+    if (!m) return fail(TNSIM_EINVAL, "state is NULL");
+    if (jacobi_idle_polls < 0 || jacobi_idle_polls > 0xffffffffll || mbarrier_polls < 0 ||
+        mbarrier_polls > 0x7fffffffll)
+        return fail(TNSIM_EINVAL, "poll limits must be >= 0 and fit 32 bits");
+    m->jac_spin = (unsigned)jacobi_idle_polls;
+    m->tc_spin = (int)mbarrier_polls;
+    return TNSIM_OK;
+}
+
+tnsim_status tnsim_set_device_memory_cap(int64_t bytes) {
+    if (bytes < 0) return fail(TNSIM_EINVAL, "the cap must be >= 0 (0 = none)");
+    g_dev_cap.store(bytes);
+    return TNSIM_OK;
+}
+
+int64_t tnsim_device_bytes_held(void) { return g_dev_held.load(); }
 
 tnsim_status tnsim_set_jacobi_config(tnsim_mps* m, int32_t cfg) {
     if (!m) return fail(TNSIM_EINVAL, "state is NULL");

@@ -76,7 +76,10 @@ struct GateDesc {
     // QR preconditioning (k_qr.cu): for m == n the Jacobi runs on R^H of theta = Q R; the
     // left site becomes theta W' S^-2 and the right site the conjugated Jacobi columns
     int qr;
-    int pad_;
+    // polls of a bounded mbarrier wait in the tensor-core contraction before it gives up
+    // (0 = the kernel's default); the CTA then drains its copies in flight and reports
+    // status 5 (ETIMEOUT)
+    int wait_polls;
 };
 
 // largest m of a QR-preconditioned gate (its panel of columns sits in shared memory)
@@ -106,9 +109,11 @@ cudaError_t launch_theta(const GateDesc* d, int n_gates, int chiL_max, int chiR_
 constexpr int kJacobiConfigs = 4;
 // n_lead: how many leading descriptors (sorted by decreasing size) share the first one's
 // size; the persistent CTAs start spread over them (0: over all gates).
+// spin_limit: idle polls without progress before an idle CTA gives up (0 = default).
 template <typename T>
 cudaError_t launch_jacobi(const GateDesc* d, int n_gates, int m_max, int n_max, double tol,
-                          int max_sweeps, JacobiCtl* ctl, cudaStream_t s, int cfg = 0, int n_lead = 0);
+                          int max_sweeps, JacobiCtl* ctl, cudaStream_t s, int cfg = 0, int n_lead = 0,
+                          unsigned spin_limit = 0);
 template <typename T>
 cudaError_t launch_truncate(const GateDesc* d, int n_gates, cudaStream_t s);
 template <typename T>

@@ -148,10 +148,14 @@ extern "C" tnsim_status tnsim_two_site_update_noalloc(
     NA_TRY(launch_right<float>(dd, 1, kcap, 2 * chi_r, st));
     GateOut o;
     NA_TRY(cudaMemcpyAsync(&o, base + OFF_OUT, sizeof(o), cudaMemcpyDeviceToHost, st));
+    // the kept count is known only after the sync: copy every entry that can be kept
+    // (k <= kcap) on the caller's stream, then clear the ones past k on the host
+    if (s_out) NA_TRY(cudaMemcpyAsync(s_out, base + OFF_SPEC, sizeof(double) * kcap, cudaMemcpyDeviceToHost, st));
     NA_TRY(cudaStreamSynchronize(st));
     *k_out = o.k;
     if (eps_out) *eps_out = o.eps;
-    if (s_out) NA_TRY(cudaMemcpy(s_out, base + OFF_SPEC, sizeof(double) * o.k, cudaMemcpyDeviceToHost));
+    if (s_out)
+        for (int j = std::max(o.k, 0); j < chi_max; ++j) s_out[j] = 0.0;
 #undef NA_TRY
     if (o.status == 5) return na_fail(TNSIM_ETIMEOUT, "the Jacobi kernel saw no progress (update incomplete)");
     if (o.status) return na_fail(TNSIM_ENOCONV, "the Jacobi SVD reached its sweep cap (update applied)");

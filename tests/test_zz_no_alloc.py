@@ -1,4 +1,4 @@
-"""tnsim_two_site_update_noalloc against tnsim_apply_layer on the same input.
+"""tnsim_two_site_update_noalloc against tnsim_apply_layer and the FP64 oracle.
 
 The no-allocation entry point exists for callers that may not let the library call
 cudaMalloc (a plugin inside an application whose memory pool owns the device, a
@@ -7,7 +7,10 @@ in a fixed scratch array compiled into the library, so this test checks that two
 calls in a row -- the second one smaller than the first, on the leftovers of the
 first -- give the same update as the ordinary handle-based path, within the
 complex64 tolerances of the other GPU tests (singular values within 1e-5 of s_max,
-the gauge-invariant two-site block within 1e-5 relative).
+the gauge-invariant two-site block within 1e-5 relative), and the update of the
+oracle (oracle.mps.apply_2q on the same complex64-rounded sites): singular values
+within 1e-5 of s_max, the discarded weight within 1e-6, and the two-site block at
+1 - F <= 1e-6.
 """
 import numpy as np
 import pytest
@@ -28,6 +31,7 @@ def test_noalloc_update_matches_layer_path_twice():
     g.build()
     import paper_2601_04422_gb300 as T
     import workloads as W
+    from oracle import mps as om
 
     n, q = 16, 7
     for call, (chi, chi_max, seed) in enumerate(((128, 128, 11), (32, 32, 12))):
@@ -65,6 +69,16 @@ def test_noalloc_update_matches_layer_path_twice():
         blk = np.einsum("lxb,byr->lxyr", a_new, b_new)
         blk_ref = np.einsum("lxb,byr->lxyr", out[q], out[q + 1])
         assert np.linalg.norm(blk - blk_ref) / np.linalg.norm(blk_ref) <= 1e-5
+
+        # the oracle's update of the same complex64-rounded sites
+        ref = om.MPS([s_.astype(np.complex64).astype(np.complex128) for s_ in sites])
+        rec = om.apply_2q(ref, q, gate, chi_max)
+        assert k == rec.k
+        assert np.max(np.abs(s - rec.s_kept)) / rec.s_kept[0] <= 1e-5
+        assert abs(eps - rec.eps) <= 1e-6
+        blk_o = np.einsum("lxb,byr->lxyr", ref.sites[q], ref.sites[q + 1])
+        f = abs(np.vdot(blk_o, blk)) ** 2 / (np.vdot(blk_o, blk_o).real * np.vdot(blk, blk).real)
+        assert 1.0 - f <= 1e-6
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch():
