@@ -16,8 +16,11 @@ grad   -- the reverse-mode gradient of an energy through the layered simulation
           (the exact derivative of the truncated updates), pinned by finite
           differences of the dense and of the truncated energies.
 
-Every function is complex128 / float64.  The singular value decomposition step
-calls LAPACK through ``numpy.linalg.svd`` (a library primitive).
+Every function is complex128 / float64, except ``mps.apply_2q_single_precision``,
+which rounds the stored sites to complex64 and contracts in complex64 around an
+exact FP64 SVD: the precision floor that no complex64 path can go below.  The
+singular value decomposition step calls LAPACK through ``numpy.linalg.svd`` (a
+library primitive).
 
 Parity status: every function is pinned by ``tests/test_oracle_*.py`` against
 the dense simulator, closed forms (GHZ, QFT of a basis state), invariants or

@@ -188,14 +188,54 @@ def apply_2q_canonical(mps: MPS, q: int, g: np.ndarray, chi_max: int, cutoff: fl
     return GateRecord(q, s, k, disc, s_kept)
 
 
+def apply_2q_single_precision(mps: MPS, q: int, g: np.ndarray, chi_max: int, cutoff: float = 0.0,
+                              renormalize: bool = True) -> GateRecord:
+    """apply_2q with the storage and contraction precision of a complex64 run and an
+    exact SVD: the precision floor of any complex64 path.
+
+    Both sites are read as complex64, the merge (Fig. 2) is a complex64 matrix product
+    and the gate (Eq. 1) a complex64 contraction, both accumulating in single
+    precision; theta is then decomposed in FP64 (LAPACK), truncated with the
+    single-precision zero threshold (eps = eps_32), and the new sites are rounded to
+    complex64.  Comparing a complex64 path with apply_2q measures its whole error;
+    comparing this function with apply_2q measures the part that no SVD, however
+    accurate, can remove."""
+    a = mps.sites[q].astype(np.complex64)
+    b = mps.sites[q + 1].astype(np.complex64)
+    chi_l, chi_m, chi_r = a.shape[0], a.shape[2], b.shape[2]
+    merged = (a.reshape(2 * chi_l, chi_m) @ b.reshape(chi_m, 2 * chi_r)).reshape(chi_l, 2, 2, chi_r)
+    G = g.astype(np.complex64).reshape(2, 2, 2, 2)
+    theta = np.einsum("abcd,lcdr->labr", G, merged)
+    mat = theta.reshape(2 * chi_l, 2 * chi_r).astype(np.complex128)
+    u, s, vh = np.linalg.svd(mat, full_matrices=False)
+    k, disc = truncation_rank(s, mat.shape[0], mat.shape[1], chi_max, cutoff,
+                              eps=float(np.finfo(np.float32).eps))
+    s_kept = s[:k].copy()
+    if renormalize:
+        kept = float(np.sum(s_kept ** 2))
+        if kept > 0.0:
+            s_kept *= np.sqrt(float(np.sum(s * s)) / kept)
+    left = u[:, :k].reshape(chi_l, 2, k)
+    right = (s_kept[:, None] * vh[:k, :]).reshape(k, 2, chi_r)
+    mps.sites[q] = left.astype(np.complex64).astype(np.complex128)
+    mps.sites[q + 1] = right.astype(np.complex64).astype(np.complex128)
+    mps.spectrum[q + 1] = s_kept.copy()
+    return GateRecord(q, s, k, disc, s_kept)
+
+
 def apply_layer(mps: MPS, layer, chi_max: int, cutoff: float = 0.0,
-                renormalize: bool = True, canonical: bool = False) -> List[GateRecord]:
+                renormalize: bool = True, canonical: bool = False, single: bool = False) -> List[GateRecord]:
     """One layer: its one-qubit gates on every qubit, then its disjoint two-qubit gates
-    (apply_2q, or apply_2q_canonical when ``canonical``)."""
+    (apply_2q, apply_2q_canonical when ``canonical``, or apply_2q_single_precision when
+    ``single``)."""
     if layer.u1 is not None:
         for q in range(mps.n):
             apply_1q(mps, q, layer.u1[q])
+            if single:   # complex64 storage
+                mps.sites[q] = mps.sites[q].astype(np.complex64).astype(np.complex128)
     upd = apply_2q_canonical if canonical else apply_2q
+    if single:
+        upd = apply_2q_single_precision
     recs = []
     for q, g in zip(layer.pairs, layer.g4):
         recs.append(upd(mps, int(q), g, chi_max, cutoff, renormalize))
@@ -256,11 +296,11 @@ def run_ops(n: int, ops, chi_max: int, cutoff: float = 0.0, renormalize: bool = 
 
 
 def run_circuit(circuit, chi_max: int, cutoff: float = 0.0, renormalize: bool = True,
-                mps: Optional[MPS] = None, canonical: bool = False):
+                mps: Optional[MPS] = None, canonical: bool = False, single: bool = False):
     """Run every layer from |0...0> (or from ``mps``); returns (mps, records per layer)."""
     if mps is None:
         mps = zero_state(circuit.n_qubits)
-    recs = [apply_layer(mps, layer, chi_max, cutoff, renormalize, canonical) for layer in circuit.layers]
+    recs = [apply_layer(mps, layer, chi_max, cutoff, renormalize, canonical, single) for layer in circuit.layers]
     return mps, recs
 
 

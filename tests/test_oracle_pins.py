@@ -294,3 +294,34 @@ def test_svd_step_properties():
     assert np.max(np.abs(u.conj().T @ u - np.eye(10))) < 1e-13
     assert np.max(np.abs(vh @ vh.conj().T - np.eye(10))) < 1e-13
     assert np.max(np.abs((u * s) @ vh - theta)) < 1e-13
+
+
+# ----------------------------------------------------------------- the complex64 precision floor
+
+
+def test_single_precision_floor_variant():
+    """apply_2q_single_precision: the paper's update with complex64 storage and
+    contraction around an exact SVD.  Pins: exact on data whose products are exact in
+    single precision (CX on basis states), within single-precision rounding of the
+    dense state vector on the exact 10-qubit circuit (and measurably not FP64, so
+    the rounding is really applied), and every stored site representable in complex64."""
+    # CX (control = left) on |10>: theta entries are 0 and 1, so nothing rounds
+    for single in (False, True):
+        m = om.zero_state(4)
+        om.apply_1q(m, 1, W.gate_x())
+        upd = om.apply_2q_single_precision if single else om.apply_2q
+        upd(m, 1, W.gate_cx(), 4)
+        bits = np.array([[0, 1, 1, 0], [0, 1, 0, 0]], dtype=np.uint8)
+        amps = om.amplitudes(m, bits)
+        assert abs(amps[0] - 1) < 1e-15 and abs(amps[1]) < 1e-15
+    # the exact C1 circuit, layer by layer
+    circ, p = W.config_c1(2)
+    m64, _ = om.run_circuit(circ, p["chi_max"])
+    m32, _ = om.run_circuit(circ, p["chi_max"], single=True)
+    psi = dense.run_circuit(circ)
+    d32 = om.to_dense(m32)
+    err = np.linalg.norm(d32 - psi) / np.linalg.norm(psi)
+    assert 1e-9 < err < 1e-5
+    assert np.linalg.norm(om.to_dense(m64) - psi) < 1e-12
+    for s in m32.sites:
+        assert np.array_equal(s, s.astype(np.complex64).astype(np.complex128))
