@@ -76,6 +76,31 @@ def energy(mps: M.MPS, paulis: Sequence[str], coeffs: Sequence[float]) -> float:
     return float(num / M.norm2(mps))
 
 
+def energy_local(mps: M.MPS, paulis: Sequence[str], coeffs: Sequence[float]) -> float:
+    """The same E as ``energy``, with each Pauli string contracted only over its support:
+    <P> = L_lo . (sites lo..hi with their operators) . R_{hi+1}, where L and R are the
+    left / right environments of the identity (every site outside the support carries
+    the identity, so the rest of the chain is L and R)."""
+    n = mps.n
+    eye = [PAULI["I"]] * n
+    L0, R0 = _env_left(mps.sites, eye), _env_right(mps.sites, eye)
+    nrm = float(L0[n][0, 0].real)
+    num = 0.0
+    for p, c in zip(paulis, coeffs):
+        sup = [q for q, ch in enumerate(p) if ch != "I"]
+        if not sup:
+            num += c * nrm
+            continue
+        e = L0[sup[0]]
+        for q in range(sup[0], sup[-1] + 1):
+            a = mps.sites[q]
+            op = PAULI[p[q]]
+            # e'[a', b'] = sum conj(A[x, p, a']) op[p, p'] e[x, y] A[y, p', b']
+            e = np.einsum("xpa,pq,xy,yqb->ab", a.conj(), op, e, a, optimize=True)
+        num += c * float(np.einsum("ab,ab->", e, R0[sup[-1] + 1]).real)
+    return float(num / nrm)
+
+
 def run(n: int, layers, axes: List[str], theta: List[np.ndarray], chi_max: int, cutoff: float = 0.0,
         renormalize: bool = True):
     """Forward pass; layers[L] = (pairs, g4[n2,4,4]); returns (final mps, checkpoints before each layer)."""
@@ -146,7 +171,7 @@ def final_adjoint(mps: M.MPS, paulis: Sequence[str], coeffs: Sequence[float]):
 # backward through the steps
 
 
-def truncation_backward(T, uk, y, s, nz, u_all, ub, yb, tau: float = 0.0, broaden: float = 1e-24):
+def truncation_backward(T, uk, y, s, nz, u_all, ub, yb, tau: float = 0.0, broaden: float = 1e-32):
     """Tb for the truncated update T -> (U, Y): U (m x k) the kept left singular vectors
     of T as the forward produced them, Y = U^H T, given Ub and the total Yb.
 
@@ -169,9 +194,13 @@ def truncation_backward(T, uk, y, s, nz, u_all, ub, yb, tau: float = 0.0, broade
     avoids dividing the rounding of (I - P) T Yb^H by s_j.  tau > 0: kept directions with
     s_j <= tau s_max get no inverse factors (a pseudo-inverse cutoff): their rows of
     S_k^-2 Y and their columns of G are zero.  tau = 0 is the exact derivative.
-    broaden: G_lj = d / (d^2 + broaden s_max^4) with d = s_j^2 - s_l^2 (Lorentzian
-    broadening of the cut's denominators; at a degenerate cut the truncated map is not
-    differentiable and this keeps the result finite)."""
+    broaden: G_lj = d / (d^2 + broaden s_max^2 (s_j + s_l)^2) with d = s_j^2 - s_l^2, a
+    Lorentzian broadening of the cut's denominators on the scale of the rounding error
+    of d: singular values computed with absolute errors ~ eps s_max give |delta d| ~
+    eps s_max (s_j + s_l), so broaden = eps^2 regularises exactly the pairs whose
+    denominator is not resolved, and leaves small but separated singular values
+    alone.  At a degenerate cut the truncated map is not differentiable and this
+    keeps the result finite."""
     k = uk.shape[1]
     sk = s[:k]
     ud, sd = u_all[:, k:nz], s[k:nz]
@@ -183,7 +212,7 @@ def truncation_backward(T, uk, y, s, nz, u_all, ub, yb, tau: float = 0.0, broade
     tb += (ub - p_all @ ub) @ (y * inv2[:, None])
     if nz > k:
         d = sk[None, :] ** 2 - sd[:, None] ** 2                 # [l, j] = s_j^2 - s_l^2
-        eps_b = broaden * sk[0] ** 4
+        eps_b = broaden * sk[0] ** 2 * (sk[None, :] + sd[:, None]) ** 2
         G = (d / (d * d + eps_b)) * live[None, :]
         Z = ud @ (G * (ud.conj().T @ ut)) @ uk.conj().T
         tb += (Z + Z.conj().T) @ T
@@ -191,7 +220,7 @@ def truncation_backward(T, uk, y, s, nz, u_all, ub, yb, tau: float = 0.0, broade
 
 
 def gate_backward(a, b, g4, ul, ur, a_new, b_new, ab_new, bb_new, renormalize, tau: float = 0.0,
-                  broaden: float = 1e-24):
+                  broaden: float = 1e-32):
     """Backward of one two-qubit update on pre-gate sites a, b (before the one-qubit gates
     ul, ur of the layer, None = identity) that produced a_new (U) and b_new (c Y, c the
     renormalisation factor |T|_F / |Y|_F).  ab_new, bb_new: adjoints of the new sites.
@@ -234,7 +263,7 @@ def gate_backward(a, b, g4, ul, ur, a_new, b_new, ab_new, bb_new, renormalize, t
 
 
 def grad(n: int, layers, axes: List[str], theta: List[np.ndarray], paulis, coeffs, chi_max: int,
-         cutoff: float = 0.0, renormalize: bool = True, tau: float = 0.0, broaden: float = 1e-24):
+         cutoff: float = 0.0, renormalize: bool = True, tau: float = 0.0, broaden: float = 1e-32):
     """(E, [dE/dtheta_L]) for the layered circuit; theta[L] has shape [n, len(axes[L])]."""
     final, ckpt = run(n, layers, axes, theta, chi_max, cutoff, renormalize)
     e, abar = final_adjoint(final, paulis, coeffs)

@@ -7,9 +7,12 @@ below tau s_max get no inverse factors).  Tolerances: complex128 within 1e-9 of 
 largest component (energy 1e-12); complex64 within 2e-3 (energy 1e-5 relative).
 At a binding cut with degenerate singular values the truncated energy is not
 differentiable (which of the degenerate vectors is kept depends on rounding); the
-50-qubit workload has such cuts, so there the energy and the median component are
-compared.
+50-qubit workload runs with a 1e-10 discarded-weight cutoff that drops the
+numerically zero directions (tests/hea_workload.py), and there every component is
+compared, and the oracle is pinned by finite differences at that workload.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -56,7 +59,7 @@ def test_complex128_against_the_oracle(T, chi, renorm):
     layers, axes, theta, paulis, coeffs = _hea(n, 4, seed=3, sigma=0.5)
     e, g = T.tnsim_grad(n, layers, axes, theta, paulis, coeffs, T.TNSIM_C128, _params(T, T.TNSIM_C128, chi, renorm))
     e_ref, g_ref = OG.grad(n, layers, axes, theta, paulis, coeffs, chi_max=chi, renormalize=renorm, tau=TAU64,
-                           broaden=TAU64 ** 2)
+                           broaden=TAU64 ** 4)
     assert abs(e - e_ref) < 1e-12
     gf, rf = _flat(g), _flat(g_ref)
     assert np.max(np.abs(gf - rf)) <= 1e-9 * np.max(np.abs(rf))
@@ -80,30 +83,74 @@ def test_complex128_against_finite_differences_of_its_own_energy(T):
 def test_complex64_against_the_oracle(T, n, chi):
     layers, axes, theta, paulis, coeffs = _hea(n, 4, seed=7, sigma=0.5)
     e, g = T.tnsim_grad(n, layers, axes, theta, paulis, coeffs, T.TNSIM_C64, _params(T, T.TNSIM_C64, chi))
-    e_ref, g_ref = OG.grad(n, layers, axes, theta, paulis, coeffs, chi_max=chi, tau=TAU32, broaden=TAU32 ** 2)
+    e_ref, g_ref = OG.grad(n, layers, axes, theta, paulis, coeffs, chi_max=chi, tau=TAU32, broaden=TAU32 ** 4)
     assert abs(e - e_ref) < 1e-5 * max(1.0, abs(e_ref))
     gf, rf = _flat(g), _flat(g_ref)
     assert np.max(np.abs(gf - rf)) <= 2e-3 * np.max(np.abs(rf))
 
 
 @pytest.mark.slow
-def test_hea_50_qubits_10_layers_chi64(T):
-    """The differentiation workload: 50 qubits, 10 HEA layers (1000 angles, sigma 0.3),
-    chi_max 64, H = sum Z_i Z_{i+1} + 0.5 sum X_i.  This run truncates at cuts with
-    degenerate singular values (relative gaps down to 1e-14), where the Jacobi SVD and
-    LAPACK keep different vectors: the two states differ by about 1e-6 in energy and
-    the gradient is not pinned there.  Checked: the energy within 1e-5 relative, and the
-    median component of the gradient within 1e-3 of the largest (about 80 % (complex128)
-    and 60 % (complex64) of the components agree that well)."""
-    n = 50
-    layers, axes, theta, paulis, coeffs = _hea(n, 10, seed=1, sigma=0.3)
-    for dt, tau in ((T.TNSIM_C128, TAU64), (T.TNSIM_C64, TAU32)):
-        e, g = T.tnsim_grad(n, layers, axes, theta, paulis, coeffs, dt, _params(T, dt, 64))
-        e_ref, g_ref = OG.grad(n, layers, axes, theta, paulis, coeffs, chi_max=64, tau=tau, broaden=tau ** 2)
+def test_hea_workload_gradient(T):
+    """The differentiation workload (tests/hea_workload.py: 50 qubits, 10 HEA layers,
+    1000 angles, chi_max 64, cutoff 1e-10, seed 2):
+      1. the oracle's exact gradient against central finite differences (h = 1e-4,
+         FP64) of its own energy on 32 seeded angles, within 1e-4 of the largest
+         component (the differences straddle cutoff crossings of the bond dimension,
+         each a jump of ~1e-10 in the energy);
+      2. complex128 on the GPU: the energy within 1e-10 relative and every one of the
+         1000 components within 1e-7 of the largest, against the oracle with the same
+         regularisation (pseudo-inverse cutoff sqrt(eps) s_max, broadening eps^2);
+         central differences of the GPU's own energy on 4 angles within 1e-6;
+      3. complex64 on the GPU: the energy within 1e-5 relative and every component
+         within 1e-2 of the largest (oracle with the FP32 regularisation)."""
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    import hea_workload as H
+
+    n = H.N
+    layers, axes, theta, paulis, coeffs = H.hea()
+    rng = np.random.default_rng(7)
+    picks = [(2 * int(rng.integers(H.N_LAYERS)), int(rng.integers(n)), int(rng.integers(2))) for _ in range(32)]
+    h = 1e-4
+    args = [(L, q, j, s * h) for (L, q, j) in picks for s in (1.0, -1.0)]
+    # one BLAS thread per worker process (the variables are read when a worker loads numpy)
+    one = {k: "1" for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    saved = {k: os.environ.get(k) for k in one}
+    os.environ.update(one)
+    try:
+        with ProcessPoolExecutor(max_workers=max(1, min(16, os.cpu_count() or 1)),
+                                 mp_context=mp.get_context("spawn")) as ex:
+            es = list(ex.map(H.energy_shifted, args))
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    fd = np.array([(es[2 * i] - es[2 * i + 1]) / (2 * h) for i in range(len(picks))])
+    e_ex, g_ex = OG.grad(n, layers, axes, theta, paulis, coeffs, chi_max=H.CHI, cutoff=H.CUTOFF)
+    gmax = np.max(np.abs(_flat(g_ex)))
+    want = np.array([g_ex[L][q, j] for (L, q, j) in picks])
+    assert np.max(np.abs(fd - want)) <= 1e-4 * gmax, np.max(np.abs(fd - want)) / gmax
+
+    for dt, tau, tol_e, tol_g in ((T.TNSIM_C128, TAU64, 1e-10, 1e-7), (T.TNSIM_C64, TAU32, 1e-5, 1e-2)):
+        p = _params(T, dt, H.CHI)
+        p.cutoff = H.CUTOFF
+        e, g = T.tnsim_grad(n, layers, axes, theta, paulis, coeffs, dt, p)
+        e_ref, g_ref = OG.grad(n, layers, axes, theta, paulis, coeffs, chi_max=H.CHI, cutoff=H.CUTOFF, tau=tau,
+                               broaden=tau ** 4)
         gf, rf = _flat(g), _flat(g_ref)
         assert gf.size == 1000 and np.all(np.isfinite(gf))
-        assert abs(e - e_ref) < 1e-5 * abs(e_ref)
-        assert np.median(np.abs(gf - rf)) <= 1e-3 * np.max(np.abs(rf))
+        assert abs(e - e_ref) <= tol_e * abs(e_ref), (dt, e, e_ref)
+        err = np.max(np.abs(gf - rf)) / np.max(np.abs(rf))
+        assert err <= tol_g, (dt, err)
+        if dt == T.TNSIM_C128:
+            for (L, q, j) in picks[:4]:
+                tp = [t.copy() for t in theta]; tm = [t.copy() for t in theta]
+                tp[L][q, j] += h; tm[L][q, j] -= h
+                ep, _ = T.tnsim_grad(n, layers, axes, tp, paulis, coeffs, dt, p)
+                em, _ = T.tnsim_grad(n, layers, axes, tm, paulis, coeffs, dt, p)
+                assert abs((ep - em) / (2 * h) - g[L][q, j]) <= 1e-6 * np.max(np.abs(rf))
 
 
 def test_torch_autograd_function(T):

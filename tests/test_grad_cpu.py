@@ -115,3 +115,19 @@ def test_rotation_convention():
         assert np.allclose(G.rotation("X", t), W.gate_rx(t), atol=1e-15)
         assert np.allclose(G.rotation("Y", t), W.gate_ry(t), atol=1e-15)
         assert np.allclose(G.rotation("Z", t), W.gate_rz(t), atol=1e-15)
+
+
+def test_energy_local_equals_full_transfer():
+    """energy_local (each string contracted over its support between identity
+    environments) equals the full-chain energy on a random, unnormalised MPS."""
+    rng = np.random.default_rng(31)
+    n = 7
+    dims = [1, 2, 4, 5, 5, 4, 2, 1]
+    sites = [rng.standard_normal((dims[q], 2, dims[q + 1])) + 1j * rng.standard_normal((dims[q], 2, dims[q + 1]))
+             for q in range(n)]
+    m = M.MPS(sites)
+    paulis = ["".join(rng.choice(list("IXYZ"), size=n)) for _ in range(12)]
+    paulis += ["I" * n, "Z" + "I" * (n - 1), "I" * (n - 1) + "X", "IIZZIII", "XIIIIIY"]
+    coeffs = rng.standard_normal(len(paulis))
+    assert abs(G.energy_local(m, paulis, coeffs) - G.energy(m, paulis, coeffs)) < 1e-12 * max(
+        1.0, abs(G.energy(m, paulis, coeffs)))
