@@ -6,13 +6,20 @@ arithmetic), batched schedule.  The state is first evolved (untimed) until the
 interior bonds saturate at chi = 256; then W warm-up layers, then K timed layers.
 A step is one brickwork layer (49 or 50 gates).  The inputs (gates) sit in HBM
 before the timed region starts; the state (88 MB) and per-layer workspace
-(2 x 2 MiB per gate) together exceed the 126 MB L2.
+(2 x 2 MiB per gate) together exceed the 126 MB L2.  Nothing but the layers runs
+in the timed region (no per-kernel events).
 
-Also reported on the same line: the end-to-end rate through the synchronous C-ABI
-call with host gate buffers (e2e), the Jacobi kernel's fraction of the FP32 ALU
-roofline (per-kernel CUDA events recorded on the library's stream during the
-timed region), the plain per-pair complex128 GPU path on sampled gates of the same
-state, and the FP64 oracle timed on the host cores (cpu_baseline).
+Also reported on the same line:
+  e2e          the synchronous C-ABI call with host gate buffers (copies included);
+  roofline     the Jacobi kernel against the FP32 ALU peak, from per-kernel CUDA
+               events recorded in a separate pass over the next layers;
+  fidelity     1 - F of the complex64 states against the complex128 GPU path run
+               from the same start state (after one layer and after all K layers);
+  batched_c128 the complex128 path with the headline's schedule on the same layers;
+  plain_path   the plain per-pair complex128 path on one layer of the same state;
+  c4           256 independent circuits of uneven width, depth and chi_max as one
+               CUDA graph of frozen plans;
+  cpu_baseline the FP64 oracle on the host cores (all cores, and one thread).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -40,6 +47,7 @@ sys.path.insert(0, ROOT)
 METRIC = "2-qubit gates/s at χ=256 (contract+SVD+truncate), % roofline, vs plain path"
 UNIT = "2q gates/s"
 N_QUBITS, CHI, PRESAT = 100, 256, 10
+HEA_CUTOFF = 1e-10          # discarded-weight cutoff of the gradient workload
 JACOBI_SRC = os.path.join(ROOT, "paper_2601_04422_gb300", "csrc", "k_jacobi.cu")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_jacobi_chi256.md")
 
@@ -50,7 +58,13 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--plain-gates", type=int, default=4, help="gates timed on the plain c128 path")
+    ap.add_argument("--plain-gates", type=int, default=64,
+                    help="gates timed on the plain c128 path (at most one layer)")
+    ap.add_argument("--profile-layers", type=int, default=3,
+                    help="layers of the separate pass with per-kernel CUDA events")
+    ap.add_argument("--no-fidelity", dest="fidelity", action="store_false",
+                    help="skip the complex128 run from the timed region's start state")
+    ap.add_argument("--c4-circuits", type=int, default=256, help="circuits of the batched graph leg (0 = skip)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle sample")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--shots", type=int, default=1024, help="perfect-sampling shots on the saturated state")
@@ -195,21 +209,56 @@ def oracle_gate_rate(seconds: float, seed: int = 5):
     return gates / dt, gates, dt
 
 
-def host_cores():
-    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-        if os.environ.get(k):
-            try:
-                return int(os.environ[k])
-            except ValueError:
-                pass
+def host_cores() -> int:
+    """The host cores this process may run on (nproc)."""
     try:
-        from threadpoolctl import threadpool_info
-        n = [i.get("num_threads", 0) for i in threadpool_info() if i.get("user_api") == "blas"]
-        if n:
-            return max(n)
-    except Exception:
-        pass
-    return os.cpu_count()
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
+_ONE_THREAD = {k: "1" for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS",
+                                "BLIS_NUM_THREADS", "VECLIB_MAXIMUM_THREADS", "NUMEXPR_NUM_THREADS")}
+
+
+def oracle_gate_rate_one_thread(seconds: float):
+    """The same oracle sample in a child process whose BLAS/LAPACK runs on one thread
+    (the thread count of a BLAS library is fixed when it loads)."""
+    code = ("import json, sys; sys.path.insert(0, %r); import bench; "
+            "r, g, s = bench.oracle_gate_rate(%r); print(json.dumps([r, g, s]))" % (ROOT, float(seconds)))
+    env = dict(os.environ, **_ONE_THREAD)
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                         timeout=max(120.0, 10 * seconds))
+    if out.returncode != 0:
+        return None
+    r, g, s = json.loads(out.stdout.strip().splitlines()[-1])
+    return r, g, s
+
+
+def mps_overlap(sa, sb) -> complex:
+    """<a|b> of two MPS given as site lists (chi_l, 2, chi_r), by left-to-right transfer
+    matrices with BLAS matrix products (measurement only: compares two outputs of the
+    library, e.g. a complex64 and a complex128 run from the same start state)."""
+    e = np.ones((1, 1), dtype=np.complex128)
+    for a, b in zip(sa, sb):
+        nxt = np.zeros((a.shape[2], b.shape[2]), dtype=np.complex128)
+        for p in range(2):
+            nxt += a[:, p, :].conj().T @ (e @ b[:, p, :])
+        e = nxt
+    return complex(e[0, 0])
+
+
+def infidelity(sa, sb) -> float:
+    ab = mps_overlap(sa, sb)
+    return float(1.0 - abs(ab) ** 2 / (mps_overlap(sa, sa).real * mps_overlap(sb, sb).real))
+
+
+def kernels_per_layer(gemm: str, cfg: int) -> int:
+    """Kernels one batched layer launches: contraction (split + tcgen05 GEMM on the tensor
+    path), QR (configurations 2, 3), Jacobi, truncation, left site, right site, and the two
+    site kernels of the QR route."""
+    theta = 2 if gemm in ("tf32x3", "bf16x3") else 1
+    return theta + 1 + 1 + 1 + 1 + (3 if cfg & 2 else 0)
 
 
 def run_reference(args, world, rank):
@@ -244,6 +293,80 @@ def workload_config():
             "l2": "inputs larger than L2: state 88 MB + theta/W workspace 196 MB per layer"}
 
 
+def make_gates_dev(torch, dev, layers):
+    return [torch.from_numpy(np.ascontiguousarray(l.g4).view(np.float64).copy()).to(dev) for l in layers]
+
+
+def c4_leg(T, W, torch, dev, n_circ, gemm):
+    """The batching workload: n_circ independent Haar SU(4) brickwork circuits of uneven
+    width, depth and chi_max, every step a frozen plan of all states' gates, the whole run
+    captured into one CUDA graph.  The graph is replayed once untimed (warm-up, from
+    |0...0>), the states are reset to |0...0>, and one replay is timed by CUDA events."""
+    batch = W.batch_circuits(n_circ, base_seed=1000)
+    circs = [c for c, _ in batch]
+    depth = max(len(c.layers) for c in circs)
+    stream = torch.cuda.Stream(device=dev)
+    ms = [T.MPS(c.n_qubits, dtype=T.TNSIM_C64, chi_max=chi, gemm=gemm, stream=stream.cuda_stream)
+          for c, chi in batch]
+    gdev = {}
+    for i, c in enumerate(circs):
+        for t, lay in enumerate(c.layers):
+            gdev[(i, t)] = torch.from_numpy(np.ascontiguousarray(lay.g4).view(np.float64).copy()).to(dev)
+    torch.cuda.synchronize()
+    # autotune on the widest state with the largest chi_max, from its state after half its depth
+    big = max(range(n_circ), key=lambda i: (batch[i][1], circs[i].n_qubits))
+    half = len(circs[big].layers) // 2
+    for lay in circs[big].layers[:half]:
+        ms[big].apply_layer(lay)
+    lay = circs[big].layers[half]
+    choice, tune_ms = T.tnsim_autotune(ms[big].h, lay.pairs, lay.g4, reps=1)
+    for m in ms:
+        T.tnsim_set_jacobi_config(m.h, choice)
+    zero = {}
+
+    def reset():
+        for i, m in enumerate(ms):
+            n = circs[i].n_qubits
+            if n not in zero:
+                z = np.zeros((1, 2, 1), np.complex128)
+                z[0, 0, 0] = 1.0
+                zero[n] = [z] * n
+            m.import_sites(zero[n])
+
+    reset()
+    plans = []
+    for t in range(depth):
+        idx = [i for i, c in enumerate(circs) if t < len(c.layers)]
+        plans.append(T.tnsim_plan_create([ms[i].h for i in idx],
+                                         [(circs[i].layers[t].pairs, gdev[(i, t)].data_ptr(), 0) for i in idx]))
+    graph = T.tnsim_graph_create(plans)
+    t0 = time.perf_counter()
+    T.tnsim_graph_launch(graph)
+    ms[0].sync()
+    warm_s = time.perf_counter() - t0
+    reset()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    T.tnsim_graph_launch(graph)
+    e1.record(stream)
+    ms[0].sync()
+    ms_graph = e0.elapsed_time(e1)
+    gates = sum(l.n2 for c in circs for l in c.layers)
+    T.tnsim_graph_destroy(graph)
+    for pl in plans:
+        T.tnsim_plan_destroy(pl)
+    for m in ms:
+        m.close()
+    return {"value": gates / (ms_graph / 1000.0), "unit": UNIT, "gates": gates, "ms": ms_graph,
+            "circuits": n_circ, "steps": depth, "jacobi_config": int(choice),
+            "autotune_ms": [float(x) for x in tune_ms], "warmup_replay_s": warm_s,
+            "sample": f"{n_circ} Haar SU(4) brickwork circuits (width U{{16..128}}, depth U{{8..32}}, chi_max in "
+                      "{16, 32, 64, 128, 256}, seeds 1000+i), complex64, every step one frozen plan of all "
+                      "states' gates (one persistent Jacobi launch per step), all steps one CUDA graph; the "
+                      "timed replay starts from |0...0> (CUDA events around the graph launch)"}
+
+
 def run_ours(args, world, rank, local):
     import torch
     import __graft_entry__ as g
@@ -258,39 +381,38 @@ def run_ours(args, world, rank, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    depth = PRESAT + args.warmup + 2 * args.steps + 2
+    K = args.steps
+    n_prof = max(1, min(K, args.profile_layers))
+    depth = PRESAT + args.warmup + 2 * K + n_prof + 2
     circ = W.brickwork_su4(N_QUBITS, depth, seed=replica_seed(rank))
     stream = torch.cuda.Stream(device=dev)
     gemm = getattr(T, "TNSIM_GEMM_" + args.gemm.upper())
     m = T.MPS(N_QUBITS, dtype=T.TNSIM_C64, chi_max=CHI, gemm=gemm, stream=stream.cuda_stream)
-    gdev = [torch.from_numpy(np.ascontiguousarray(l.g4).view(np.float64).copy()).to(dev)
-            for l in circ.layers]
+    gdev = make_gates_dev(torch, dev, circ.layers)
     eps_dev = torch.zeros(N_QUBITS, dtype=torch.float64, device=dev)
     torch.cuda.synchronize()
 
-    def layer_dev(i):
-        T.tnsim_apply_layer_device(m.h, circ.layers[i].pairs, gdev[i].data_ptr(), 0, eps_dev.data_ptr())
+    def layer_dev(mm, i):
+        T.tnsim_apply_layer_device(mm.h, circ.layers[i].pairs, gdev[i].data_ptr(), 0, eps_dev.data_ptr())
 
     for i in range(PRESAT):
-        layer_dev(i)
+        layer_dev(m, i)
     m.sync()
     for i in range(PRESAT, PRESAT + args.warmup):
-        layer_dev(i)
+        layer_dev(m, i)
     m.sync()
     dims = m.bond_dims()
-    # autotuner: time the Jacobi launch configurations on the first timed layer's gates
-    tune_choice, tune_ms = T.tnsim_autotune(m.h, circ.layers[PRESAT + args.warmup].pairs,
-                                            circ.layers[PRESAT + args.warmup].g4, reps=2)
-    T.tnsim_last_stats(m.h)
-    T.tnsim_profile_read(m.h)
-
-    # ---- timed region: device-resident inputs
     t_lo = PRESAT + args.warmup
-    timed = list(range(t_lo, t_lo + args.steps))
+    # autotuner: time the Jacobi launch configurations on the first timed layer's gates
+    tune_choice, tune_ms = T.tnsim_autotune(m.h, circ.layers[t_lo].pairs, circ.layers[t_lo].g4, reps=2)
+    T.tnsim_last_stats(m.h)
+    start_sites = m.export_sites() if (args.fidelity and rank == 0) else None
+
+    # ---- timed region: device-resident inputs, no profiling
+    timed = list(range(t_lo, t_lo + K))
     gates_rank = sum(circ.layers[i].n2 for i in timed)
     clk = ClockSampler(local)
     clk.start()
-    T.tnsim_profile_enable(m.h, True)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -298,21 +420,21 @@ def run_ours(args, world, rank, local):
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for i in timed:
-        layer_dev(i)
+        layer_dev(m, i)
     e1.record(stream)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     ms = e0.elapsed_time(e1)
+    clocks = clk.stop()
     m.sync()
-    prof = T.tnsim_profile_read(m.h)
-    T.tnsim_profile_enable(m.h, False)
-    stats = T.tnsim_last_stats(m.h)
+    stats_timed = T.tnsim_last_stats(m.h)
+    end_sites = m.export_sites() if start_sites is not None else None
 
     # ---- end to end: the synchronous C-ABI call on host buffers (copies inside)
     e2e = None
     if not args.no_e2e:
-        host_layers = circ.layers[t_lo + args.steps: t_lo + 2 * args.steps]
+        host_layers = circ.layers[t_lo + K: t_lo + 2 * K]
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
@@ -325,7 +447,17 @@ def run_ours(args, world, rank, local):
         if dist:
             dist.barrier()
         e2e = (g_e2e, t_e2e, host_layers)
-    clocks = clk.stop()
+
+    # ---- per-kernel CUDA events, in a separate profiled pass over the next layers
+    T.tnsim_last_stats(m.h)
+    T.tnsim_profile_read(m.h)
+    T.tnsim_profile_enable(m.h, True)
+    for i in range(t_lo + 2 * K, t_lo + 2 * K + n_prof):
+        layer_dev(m, i)
+    m.sync()
+    prof = T.tnsim_profile_read(m.h)
+    T.tnsim_profile_enable(m.h, False)
+    stats = T.tnsim_last_stats(m.h)
 
     # ---- aggregate over ranks
     ms_max, gates_all = replica_reduce(ms, gates_rank, dist, dev)
@@ -341,7 +473,7 @@ def run_ours(args, world, rank, local):
                    "note": "tnsim_apply_layer on host gate arrays: gate upload, all kernels, "
                            "discarded-weight and bond-dimension read-back per step"}
 
-    # ---- roofline of the dominant kernel (the Jacobi SVD), FP32 ALU bound
+    # ---- roofline of the dominant kernel (the Jacobi SVD), FP32 ALU bound, from the profiled pass
     pk = peaks()
     jac_ms, jac_n = prof["jacobi"]
     # per examined pair-row: g = x_i^H x_j (4 FMA); per rotated pair-row: both columns updated (20 flops);
@@ -356,7 +488,8 @@ def run_ours(args, world, rank, local):
                 "traffic": (traffic if traffic is not None else None),
                 "peak_src": f"derived: 152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz ({pk['src']} max clock)",
                 "algorithmic_flops_per_launch": flops / max(jac_n, 1),
-                "avg_launch_ms": jac_ms / max(jac_n, 1)}
+                "avg_launch_ms": jac_ms / max(jac_n, 1),
+                "profiled_layers": n_prof}
     # ---- whole-gate roofline time T* (contraction on the tensor pipe at the TF32 rate;
     # QR preconditioning, Jacobi and site product on the FP32 ALUs; site reads and writes
     # at HBM rate)
@@ -379,28 +512,80 @@ def run_ours(args, world, rank, local):
     total_k_ms = sum(v[0] for v in prof.values())
     kernels = {k: {"ms": v[0], "launches": v[1], "share": (v[0] / total_k_ms if total_k_ms else 0.0)}
                for k, v in prof.items() if v[1]}
-    launches = sum(v[1] for v in prof.values())
+    launches = kernels_per_layer(args.gemm, int(tune_choice)) * K
 
-    # ---- plain per-pair complex128 path on sampled gates of the same saturated state
+    # ---- complex128 on the same saturated state: the batched schedule (same layers as the
+    # timed region, from the same start state: also the fidelity reference) and the plain
+    # per-pair schedule
+    batched128 = fidelity = None
+    if start_sites is not None:
+        mb = T.MPS(N_QUBITS, dtype=T.TNSIM_C128, chi_max=CHI, stream=stream.cuda_stream)
+        T.tnsim_set_jacobi_config(mb.h, int(tune_choice))
+        mb.import_sites(start_sites)
+        layer_dev(mb, timed[0])
+        mb.sync()
+        one128 = mb.export_sites()
+        mb.stats()
+        nb = len(timed) - 1
+        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        b0.record(stream)
+        for i in timed[1:]:
+            layer_dev(mb, i)
+        b1.record(stream)
+        mb.sync()
+        st_b = mb.stats()
+        ms_b = b0.elapsed_time(b1)
+        end128 = mb.export_sites()
+        mb.close()
+        g_b = sum(circ.layers[i].n2 for i in timed[1:])
+        if nb > 0:
+            batched128 = {"value": g_b / (ms_b / 1000.0), "unit": UNIT, "dtype": "f64",
+                          "schedule": "batched, same launches as the headline", "layers": nb,
+                          "ms_per_layer": ms_b / nb,
+                          "jacobi_sweeps_per_gate": st_b["sweeps"] / max(st_b["gates"], 1),
+                          "sample": f"timed layers 2..{K} of the headline from the same start state, complex128 "
+                                    "(FP64 contraction and Jacobi), CUDA events"}
+        # complex64 after one layer from the start state (a scratch state)
+        m1 = T.MPS(N_QUBITS, dtype=T.TNSIM_C64, chi_max=CHI, gemm=gemm, stream=stream.cuda_stream)
+        T.tnsim_set_jacobi_config(m1.h, int(tune_choice))
+        m1.import_sites(start_sites)
+        layer_dev(m1, timed[0])
+        one64 = m1.export_sites()
+        m1.close()
+        fidelity = {"one_layer": infidelity(one64, one128), "all_timed_layers": infidelity(end_sites, end128),
+                    "layers": K, "unit": "1 - F",
+                    "note": "1 - |<a|b>|^2 / (<a|a><b|b>) of the complex64 states against the complex128 GPU path "
+                            "run from the same start state through the same layers (the first timed layer, and "
+                            "all K timed layers)"}
     plain = None
     if args.plain_gates > 0 and rank == 0:
         sites = m.export_sites()
         mp = T.MPS(N_QUBITS, dtype=T.TNSIM_C128, chi_max=CHI, schedule=T.TNSIM_SCHED_PLAIN,
                    stream=stream.cuda_stream)
+        T.tnsim_set_jacobi_config(mp.h, int(tune_choice))
         mp.import_sites(sites)
-        lay = circ.layers[t_lo + 2 * args.steps]
-        mid = len(lay.pairs) // 2
-        sel = list(range(mid - args.plain_gates // 2, mid - args.plain_gates // 2 + args.plain_gates))
-        q = lay.pairs[sel]
-        gg = lay.g4[sel]
-        chis = [int(dims[int(x)]) for x in q] + [int(dims[int(x) + 2]) for x in q]
+        lay_w = circ.layers[t_lo + 2 * K + n_prof]
+        lay = circ.layers[t_lo + 2 * K + n_prof + 1]
+        # warm-up: four gates of another layer on their own (module loads, first launches)
+        mid = len(lay_w.pairs) // 2
+        wsel = list(range(mid - 2, mid + 2))
+        T.tnsim_apply_layer(mp.h, lay_w.pairs[wsel], lay_w.g4[wsel], None)
+        mp.import_sites(sites)
+        sel = list(range(min(args.plain_gates, lay.n2)))
+        gp = torch.from_numpy(np.ascontiguousarray(lay.g4[sel]).view(np.float64).copy()).to(dev)
+        mp.stats()
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        T.tnsim_apply_layer(mp.h, q, gg, None)
-        tp = time.perf_counter() - t0
-        st_p = T.tnsim_last_stats(mp.h)
-        plain = {"value": len(sel) / tp, "unit": UNIT, "dtype": "f64", "schedule": "one pair per launch",
-                 "sample": f"{len(sel)} gates of one layer at chi_L, chi_R in {sorted(set(chis))}",
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        T.tnsim_apply_layer_device(mp.h, lay.pairs[sel], gp.data_ptr(), 0, 0)
+        p1.record(stream)
+        mp.sync()
+        tp = p0.elapsed_time(p1) / 1000.0
+        st_p = mp.stats()
+        chis = sorted({int(dims[int(x)]) for x in lay.pairs[sel]} | {int(dims[int(x) + 2]) for x in lay.pairs[sel]})
+        plain = {"value": len(sel) / tp, "unit": UNIT, "dtype": "f64", "schedule": "one pair per launch sequence",
+                 "sample": f"{len(sel)} gates of one layer of the saturated state (chi_L, chi_R in {chis}), after "
+                           "a 4-gate warm-up, CUDA events on the library's stream",
                  "jacobi_sweeps_per_gate": st_p["sweeps"] / max(st_p["gates"], 1)}
         mp.close()
 
@@ -436,12 +621,13 @@ def run_ours(args, world, rank, local):
                         "sample": f"{args.shots} bitstrings of the saturated {N_QUBITS}-qubit chi {CHI} state, "
                                   "one synchronous tnsim_sample call (right environments, uniforms upload "
                                   "and bit read-back included)"}
+    m.close()
 
     # ---- reverse-mode energy gradient (tnsim_grad) of the 50-qubit, 10-layer HEA at chi 64
     grad_obj = None
     if args.grad_reps > 0 and rank == 0:
         nq = 50
-        hcirc, hang = W.hea_circuit(nq, 10, seed=1, sigma=0.3)
+        hcirc, hang = W.hea_circuit(nq, 10, seed=2, sigma=0.3)
         hl = [(l.pairs, l.g4) for l in hcirc.layers]
         hax = ["YZ" if i % 2 == 0 else "" for i in range(len(hl))]
         hth = [hang[i // 2] if i % 2 == 0 else np.zeros((nq, 0)) for i in range(len(hl))]
@@ -450,6 +636,7 @@ def run_ours(args, world, rank, local):
         hc = [1.0] * (nq - 1) + [0.5] * nq
         gp = T.tnsim_params_default(T.TNSIM_C64)
         gp.chi_max = 64
+        gp.cutoff = HEA_CUTOFF
         T.tnsim_grad(nq, hl, hax, hth, hp, hc, T.TNSIM_C64, gp, stream.cuda_stream)   # warm-up
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -459,22 +646,32 @@ def run_ours(args, world, rank, local):
         grad_obj = {"value": 1.0 / tg, "unit": "energy gradients/s (1000 angles each)", "seconds": tg,
                     "energy": ge,
                     "sample": "50-qubit hardware-efficient ansatz, 10 layers of RY RZ on every qubit and a CZ "
-                              "ladder, angles N(0, 0.3^2), chi_max 64, complex64, H = sum Z_i Z_i+1 + 0.5 sum X_i; "
-                              "one synchronous tnsim_grad call: forward with checkpoints, final adjoint, "
-                              "recompute and backward of every layer"}
+                              f"ladder, angles N(0, 0.3^2), chi_max 64, cutoff {HEA_CUTOFF:g}, complex64, "
+                              "H = sum Z_i Z_i+1 + 0.5 sum X_i; one synchronous tnsim_grad call: forward with "
+                              "checkpoints, final adjoint, recompute and backward of every layer"}
+
+    # ---- the batching workload as one CUDA graph
+    c4 = None
+    if args.c4_circuits > 0 and rank == 0:
+        c4 = c4_leg(T, W, torch, dev, args.c4_circuits, gemm)
 
     cpu = None
     if rank == 0 and world == 1 and args.cpu_seconds > 0:
         r, gcount, secs = oracle_gate_rate(args.cpu_seconds)
         cpu = {"value": r, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
                "sample": f"{gcount} two-qubit updates at chi_L = chi_M = chi_R = 256 on random "
-                         f"sites (numpy/LAPACK complex128 SVD), {secs:.1f} s"}
+                         f"sites (numpy/LAPACK complex128 SVD, BLAS threads on every core), {secs:.1f} s"}
+        one = oracle_gate_rate_one_thread(args.cpu_seconds)
+        if one is not None:
+            cpu["single_thread"] = {"value": one[0], "unit": UNIT, "cores": 1,
+                                    "sample": f"{one[1]} updates, same sample, BLAS/LAPACK on one thread, "
+                                              f"{one[2]:.1f} s"}
 
     if rank == 0:
         cfg = workload_config()
-        cfg["gates_per_step"] = gates_all / args.steps
+        cfg["gates_per_step"] = gates_all / K
         cfg["parallelism"] = f"replicas x{world}" if world > 1 else "single GPU"
-        cfg["jacobi_sweeps_per_gate"] = stats["sweeps"] / max(stats["gates"], 1)
+        cfg["jacobi_sweeps_per_gate"] = stats_timed["sweeps"] / max(stats_timed["gates"], 1)
         cfg["jacobi_config"] = {"chosen": int(tune_choice), "autotune_ms": [float(x) for x in tune_ms],
                                 "configs": ["16-column blocks, 1 CTA/SM", "8-column blocks, 2 CTAs/SM",
                                             "16-column blocks, 1 CTA/SM, QR-preconditioned",
@@ -483,16 +680,17 @@ def run_ours(args, world, rank, local):
         cfg["contraction"] = {"fp32": "FP32 FMA (4M)", "fp32_3m": "FP32 FMA (3M)",
                               "tf32x3": "tcgen05 3xTF32, FP32 accumulate",
                               "bf16x3": "tcgen05 BF16x3, FP32 accumulate"}[args.gemm]
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+                "warmup": args.warmup, "ms_per_step": ms_max / K, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": cfg, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e_obj,
-                "gpu_launches": launches, "clocks": clocks, "plain_path": plain,
-                "vs_plain": (value / plain["value"]) if plain else None, "kernels": kernels,
-                "nonlocal": nonlocal_obj, "sampling": sampling_obj, "grad": grad_obj,
-                "path_roofline": path_roofline}
+                "gpu_launches": launches, "clocks": clocks, "fidelity": fidelity,
+                "batched_c128": batched128, "plain_path": plain,
+                "vs_plain": (value / plain["value"]) if plain else None,
+                "vs_batched_c128": (value / batched128["value"]) if batched128 else None,
+                "kernels": kernels, "c4": c4, "nonlocal": nonlocal_obj, "sampling": sampling_obj,
+                "grad": grad_obj, "path_roofline": path_roofline}
         print(json.dumps(line), flush=True)
-    m.close()
     if dist:
         dist.destroy_process_group()
 
