@@ -433,6 +433,7 @@ def run_ours(args, world, rank, local):
 
     # ---- end to end: the synchronous C-ABI call on host buffers (copies inside)
     e2e = None
+    disc_mean = None
     if not args.no_e2e:
         host_layers = circ.layers[t_lo + K: t_lo + 2 * K]
         torch.cuda.synchronize()
@@ -440,13 +441,15 @@ def run_ours(args, world, rank, local):
             dist.barrier()
         t0 = time.perf_counter()
         g_e2e = 0
+        eps_all = []
         for l in host_layers:
-            T.tnsim_apply_layer(m.h, l.pairs, l.g4, None)
+            eps_all.append(T.tnsim_apply_layer(m.h, l.pairs, l.g4, None))
             g_e2e += l.n2
         t_e2e = time.perf_counter() - t0
         if dist:
             dist.barrier()
         e2e = (g_e2e, t_e2e, host_layers)
+        disc_mean = float(np.mean(np.concatenate(eps_all)))
 
     # ---- per-kernel CUDA events, in a separate profiled pass over the next layers
     T.tnsim_last_stats(m.h)
@@ -545,18 +548,37 @@ def run_ours(args, world, rank, local):
                           "jacobi_sweeps_per_gate": st_b["sweeps"] / max(st_b["gates"], 1),
                           "sample": f"timed layers 2..{K} of the headline from the same start state, complex128 "
                                     "(FP64 contraction and Jacobi), CUDA events"}
-        # complex64 after one layer from the start state (a scratch state)
+        # per layer: the complex64 replay of the timed layers from the same start state; at the
+        # first, middle and last timed layer the complex128 path applies the same layer to the
+        # complex64 input state
         m1 = T.MPS(N_QUBITS, dtype=T.TNSIM_C64, chi_max=CHI, gemm=gemm, stream=stream.cuda_stream)
         T.tnsim_set_jacobi_config(m1.h, int(tune_choice))
         m1.import_sites(start_sites)
-        layer_dev(m1, timed[0])
-        one64 = m1.export_sites()
+        mc = T.MPS(N_QUBITS, dtype=T.TNSIM_C128, chi_max=CHI, stream=stream.cuda_stream)
+        T.tnsim_set_jacobi_config(mc.h, int(tune_choice))
+        probe = sorted({0, K // 2, K - 1})
+        per_layer = []
+        for j, i in enumerate(timed):
+            pre = m1.export_sites() if j in probe else None
+            layer_dev(m1, i)
+            if pre is not None:
+                post = m1.export_sites()
+                if j == 0:
+                    ref = one128
+                else:
+                    mc.import_sites(pre)
+                    layer_dev(mc, i)
+                    ref = mc.export_sites()
+                per_layer.append({"timed_layer": j + 1, "1-F": infidelity(post, ref)})
         m1.close()
-        fidelity = {"one_layer": infidelity(one64, one128), "all_timed_layers": infidelity(end_sites, end128),
-                    "layers": K, "unit": "1 - F",
-                    "note": "1 - |<a|b>|^2 / (<a|a><b|b>) of the complex64 states against the complex128 GPU path "
-                            "run from the same start state through the same layers (the first timed layer, and "
-                            "all K timed layers)"}
+        mc.close()
+        fidelity = {"per_layer": per_layer, "max_per_layer": max(x["1-F"] for x in per_layer),
+                    "all_timed_layers": infidelity(end_sites, end128), "layers": K, "unit": "1 - F",
+                    "note": "1 - |<a|b>|^2 / (<a|a><b|b>) against the complex128 GPU path.  per_layer: one layer "
+                            "applied by both precisions to the same complex64 input state.  all_timed_layers: both "
+                            "precisions run through all K timed layers from the same start state; the truncated "
+                            "dynamics at chi 256 amplify any difference ~3.5x per layer, so the two runs drift apart "
+                            "(the same holds between any two precisions)"}
     plain = None
     if args.plain_gates > 0 and rank == 0:
         sites = m.export_sites()
@@ -627,7 +649,7 @@ def run_ours(args, world, rank, local):
     grad_obj = None
     if args.grad_reps > 0 and rank == 0:
         nq = 50
-        hcirc, hang = W.hea_circuit(nq, 10, seed=2, sigma=0.3)
+        hcirc, hang = W.hea_circuit(nq, 10, seed=7, sigma=0.3)
         hl = [(l.pairs, l.g4) for l in hcirc.layers]
         hax = ["YZ" if i % 2 == 0 else "" for i in range(len(hl))]
         hth = [hang[i // 2] if i % 2 == 0 else np.zeros((nq, 0)) for i in range(len(hl))]
@@ -677,6 +699,7 @@ def run_ours(args, world, rank, local):
                                             "16-column blocks, 1 CTA/SM, QR-preconditioned",
                                             "8-column blocks, 2 CTAs/SM, QR-preconditioned"]}
         cfg["interior_chi"] = int(np.max(dims))
+        cfg["discarded_weight_per_gate"] = disc_mean
         cfg["contraction"] = {"fp32": "FP32 FMA (4M)", "fp32_3m": "FP32 FMA (3M)",
                               "tf32x3": "tcgen05 3xTF32, FP32 accumulate",
                               "bf16x3": "tcgen05 BF16x3, FP32 accumulate"}[args.gemm]

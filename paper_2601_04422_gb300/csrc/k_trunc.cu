@@ -1,8 +1,9 @@
 // Truncation and absorption of the two-qubit update, and the one-qubit update.
 //
-//  k_truncate : one CTA per gate.  Squared column norms of the converged W are the
-//               squared singular values (FP64 accumulation); a bitonic sort orders
-//               them descending (ties: lower column first); the kept rank is
+//  k_colnorm2 : squared column norms of the converged W (the squared singular
+//               values), FP64 accumulation, 32 columns per CTA over all gates.
+//  k_truncate : one CTA per gate.  A bitonic sort orders the squared norms
+//               descending (ties: lower column first); the kept rank is
 //                 k = max(1, min(chi_max, #{s_j > eps*max(m,n)*s_max},
 //                                smallest k with sum_{j>=k} s_j^2 <= cutoff*sum s_j^2))
 //               (Sec. II.A: truncate the bond; Sec. IV.A: "the bond dimension can be
@@ -24,24 +25,75 @@ template <> struct EpsT<double> { static constexpr double v = DBL_EPSILON; };
 
 constexpr int TR_THREADS = 512;
 constexpr int TR_MAXN = 1024;
+constexpr int CN_COLS = 32;        // columns per CTA of k_colnorm2 (8 warps, 4 columns each)
 
 // a comes after b in the sorted order (descending value, ascending index)
 __device__ __forceinline__ bool after(double ka, int ia, double kb, int ib) {
     return ka < kb || (ka == kb && ia > ib);
 }
 
+// Squared column norms of the converged W in FP64, spread over many CTAs: grid
+// (column chunks of 32, gates), one warp per column at a time, 16-byte loads.  The
+// unsorted values go to d.s2 (k_truncate sorts them in place).
+template <typename T>
+__global__ void __launch_bounds__(256) k_colnorm2(const GateDesc* __restrict__ gd) {
+    using C = typename CT<T>::type;
+    const GateDesc& d = gd[blockIdx.y];
+    const int q = d.q;
+    const int m = 2 * d.chi[q], n = 2 * d.chi[q + 2];
+    const int c0 = blockIdx.x * CN_COLS;
+    if (c0 >= n) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // m is even: a column is m / 2 (complex64) or m (complex128) 16-byte units
+    constexpr int PER = 16 / (int)sizeof(C);      // complex elements per 16-byte unit
+    const int units = m / PER;
+    for (int col = c0 + warp; col < min(c0 + CN_COLS, n); col += 8) {
+        const C* wc = (const C*)d.W + (size_t)col * m;
+        double acc = 0.0;
+        for (int u = lane; u < units; u += 32) {
+            if constexpr (sizeof(C) == 8) {
+                const float4 v = __ldcg(reinterpret_cast<const float4*>(wc) + u);
+                acc += (double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z + (double)v.w * v.w;
+            } else {
+                const double2 z = __ldcg(reinterpret_cast<const double2*>(wc) + u);
+                acc = fma(z.x, z.x, fma(z.y, z.y, acc));
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) d.s2[col] = acc;
+    }
+}
+
+// block-wide sum of one double per thread (TR_THREADS threads); every thread gets it
+__device__ __forceinline__ double tr_block_sum(double v, double* red) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+#pragma unroll 1
+    for (int w = 0; w < TR_THREADS / 32; ++w) t += red[w];
+    return t;
+}
+
+// Sort the squared norms, pick the kept rank, discarded weight and renormalisation.
+// One CTA per gate: bitonic sort (descending value, then ascending column), then
+// parallel reductions and a suffix scan of the sorted values for the cutoff rule.
 template <typename T>
 __global__ void __launch_bounds__(TR_THREADS) k_truncate(const GateDesc* __restrict__ gd) {
-    using C = typename CT<T>::type;
     const GateDesc& d = gd[blockIdx.x];
     const int q = d.q;
     const int chiL = d.chi[q], chiM = d.chi[q + 1], chiR = d.chi[q + 2];
     const int m = 2 * chiL, n = 2 * chiR;
-    const C* Wm = (const C*)d.W;
     GateOut* out = d.out;
 
     __shared__ double key[TR_MAXN];
     __shared__ int idx[TR_MAXN];
+    __shared__ double red[TR_THREADS / 32];
+    __shared__ double wsum[TR_THREADS / 32];
     __shared__ int s_k;
     __shared__ double s_scale;
 
@@ -49,18 +101,15 @@ __global__ void __launch_bounds__(TR_THREADS) k_truncate(const GateDesc* __restr
     int P2 = 1;
     while (P2 < n) P2 <<= 1;
 
-    for (int col = warp; col < n; col += TR_THREADS / 32) {
-        const C* w = Wm + (size_t)col * m;
-        double acc = 0.0;
-        for (int r = lane; r < m; r += 32) {
-            const C v = __ldcg(w + r);
-            acc = fma((double)v.x, (double)v.x, fma((double)v.y, (double)v.y, acc));
+    for (int i = tid; i < P2; i += TR_THREADS) {
+        if (i < n) {
+            key[i] = __ldcg(d.s2 + i);
+            idx[i] = i;
+        } else {
+            key[i] = -1.0;
+            idx[i] = 0x7fffffff;
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) { key[col] = acc; idx[col] = col; }
     }
-    for (int i = n + tid; i < P2; i += TR_THREADS) { key[i] = -1.0; idx[i] = 0x7fffffff; }
     __syncthreads();
 
     for (int kk = 2; kk <= P2; kk <<= 1) {
@@ -79,36 +128,54 @@ __global__ void __launch_bounds__(TR_THREADS) k_truncate(const GateDesc* __restr
         }
     }
 
-    if (tid == 0) {
-        // totals summed from the smallest value up (the order the tail sums use)
-        double total = 0.0;
-        for (int j = n - 1; j >= 0; --j) total += key[j];
-        int k = 1;
-        double eps = 0.0, scale = 1.0;
-        if (total > 0.0) {
-            const double smax = sqrt(key[0]);
-            const double thr = EpsT<T>::v * (double)max(m, n) * smax;
-            int nonzero = 0;
-            while (nonzero < n && sqrt(key[nonzero]) > thr) ++nonzero;
-            // the rank of an m x n matrix is at most min(m, n); this also bounds the
-            // new site shapes by the slot capacities
-            k = max(1, min(min(d.chi_max, nonzero), min(m, n)));
-            if (d.cutoff > 0.0) {
-                const double lim = d.cutoff * total;
-                double tail = 0.0;
-                int kk = n;
-                for (int j = n - 1; j >= 0; --j) {
-                    if (tail + key[j] <= lim) { tail += key[j]; kk = j; }
-                    else break;
-                }
-                k = max(1, min(k, kk));
-            }
-            double disc = 0.0, kept = 0.0;
-            for (int j = n - 1; j >= k; --j) disc += key[j];
-            for (int j = k - 1; j >= 0; --j) kept += key[j];
-            eps = disc / total;
-            if (d.renorm && kept > 0.0) scale = sqrt(total / kept);
+    // each thread owns up to two consecutive sorted entries: 2 tid, 2 tid + 1
+    const int j0 = 2 * tid, j1 = 2 * tid + 1;
+    const double v0 = j0 < n ? key[j0] : 0.0, v1 = j1 < n ? key[j1] : 0.0;
+    const double total = tr_block_sum(v0 + v1, red);
+    int k = 1;
+    double eps = 0.0, scale = 1.0;
+    if (total > 0.0) {
+        const double smax = sqrt(key[0]);
+        const double thr = EpsT<T>::v * (double)max(m, n) * smax;
+        // the values are sorted, so the nonzero ones are a prefix
+        const double nzc = tr_block_sum((double)((j0 < n && sqrt(v0) > thr) + (j1 < n && sqrt(v1) > thr)), red);
+        const int nonzero = (int)nzc;
+        // the rank of an m x n matrix is at most min(m, n); this also bounds the new
+        // site shapes by the slot capacities
+        k = max(1, min(min(d.chi_max, nonzero), min(m, n)));
+        // suffix sums S_j = sum_{i >= j} key[i] (a reverse inclusive scan over the thread
+        // pairs): S is non-increasing in j, so the entries with S_j > lim form a prefix
+        const double pair = v0 + v1;
+        double incl = pair;     // inclusive scan from the last thread down
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const double y = __shfl_down_sync(0xffffffffu, incl, o);
+            if (lane + o < 32) incl += y;
         }
+        __syncthreads();
+        if (lane == 0) wsum[warp] = incl;      // the warp's total (its lane 0 holds all 32)
+        __syncthreads();
+        double later = 0.0;                    // the sum of every later warp
+        for (int w = warp + 1; w < TR_THREADS / 32; ++w) later += wsum[w];
+        const double S0 = incl + later;        // S_{j0}
+        const double S1 = S0 - v0;             // S_{j1}
+        if (d.cutoff > 0.0) {
+            const double lim = d.cutoff * total;
+            const double kkc = tr_block_sum((double)((j0 < n && S0 > lim) + (j1 < n && S1 > lim)), red);
+            k = max(1, min(k, (int)kkc));
+        }
+        __syncthreads();
+        // discarded and kept weights: S_k and total - S_k
+        if (j0 == k && k < n) s_scale = S0;
+        if (j1 == k && k < n) s_scale = S1;
+        if (tid == 0 && k >= n) s_scale = 0.0;
+        __syncthreads();
+        const double disc = s_scale, kept = total - disc;
+        eps = disc / total;
+        if (d.renorm && kept > 0.0) scale = sqrt(total / kept);
+        __syncthreads();
+    }
+    if (tid == 0) {
         s_k = k;
         s_scale = scale;
         out->k = k;
@@ -132,8 +199,8 @@ __global__ void __launch_bounds__(TR_THREADS) k_truncate(const GateDesc* __restr
         if (qr_active(d, m, n)) atomicAdd(&d.stats[8], (u64)2 * (u64)n * (u64)n * (u64)n / 3);
     }
     __syncthreads();
-    const int k = s_k;
-    const double scale = s_scale;
+    k = s_k;
+    scale = s_scale;
     for (int j = tid; j < n; j += TR_THREADS) {
         d.s2[j] = key[j];
         d.perm[j] = idx[j];
@@ -142,8 +209,12 @@ __global__ void __launch_bounds__(TR_THREADS) k_truncate(const GateDesc* __restr
 }
 
 template <typename T>
-cudaError_t launch_truncate(const GateDesc* d, int n_gates, cudaStream_t s) {
+cudaError_t launch_truncate(const GateDesc* d, int n_gates, int n_max, cudaStream_t s) {
     if (n_gates <= 0) return cudaSuccess;
+    dim3 gn((n_max + CN_COLS - 1) / CN_COLS, n_gates, 1);
+    k_colnorm2<T><<<gn, 256, 0, s>>>(d);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
     k_truncate<T><<<n_gates, TR_THREADS, 0, s>>>(d);
     return cudaGetLastError();
 }
@@ -229,8 +300,8 @@ cudaError_t launch_site1q(const Site1Desc* d, int n_sites, int cap_lr, cudaStrea
     return cudaGetLastError();
 }
 
-template cudaError_t launch_truncate<float>(const GateDesc*, int, cudaStream_t);
-template cudaError_t launch_truncate<double>(const GateDesc*, int, cudaStream_t);
+template cudaError_t launch_truncate<float>(const GateDesc*, int, int, cudaStream_t);
+template cudaError_t launch_truncate<double>(const GateDesc*, int, int, cudaStream_t);
 template cudaError_t launch_left<float>(const GateDesc*, int, int, int, cudaStream_t);
 template cudaError_t launch_left<double>(const GateDesc*, int, int, int, cudaStream_t);
 template cudaError_t launch_site1q<float>(const Site1Desc*, int, int, cudaStream_t);

@@ -356,7 +356,7 @@ tnsim_status launch_gates(cudaStream_t st, const std::vector<GateJob>& jobs, con
                               leading_jobs(jobs, false), pm->jac_spin));
     prof_end(pm, st, TNSIM_K_JACOBI, ev);
     ev = prof_begin(pm, st);
-    CUDA_TRY(launch_truncate<T>(d_desc, ng, st));
+    CUDA_TRY(launch_truncate<T>(d_desc, ng, n_max, st));
     prof_end(pm, st, TNSIM_K_TRUNCATE, ev);
     ev = prof_begin(pm, st);
     CUDA_TRY(launch_left<T>(d_desc, ng, m_max, k_max, st));
@@ -1040,7 +1040,7 @@ tnsim_status tnsim_plan_launch(tnsim_plan* p) {
         if (p->qr) CUDA_TRY(launch_qr<double>(p->d_desc, ng, m_max, st));
         CUDA_TRY(launch_jacobi<double>(p->d_desc, ng, m_max, n_max, p->tol, p->sweeps, p->d_ctl, st, p->jac_cfg,
                                        p->lead, p->jac_spin));
-        CUDA_TRY(launch_truncate<double>(p->d_desc, ng, st));
+        CUDA_TRY(launch_truncate<double>(p->d_desc, ng, n_max, st));
         CUDA_TRY(launch_left<double>(p->d_desc, ng, m_max, p->k_max, st));
         CUDA_TRY(launch_right<double>(p->d_desc, ng, p->k_max, n_max, st));
         if (p->canon) CUDA_TRY(launch_left_canon<double>(p->d_desc, ng, m_max, p->k_max, st));
@@ -1053,7 +1053,7 @@ tnsim_status tnsim_plan_launch(tnsim_plan* p) {
         if (p->qr) CUDA_TRY(launch_qr<float>(p->d_desc, ng, m_max, st));
         CUDA_TRY(launch_jacobi<float>(p->d_desc, ng, m_max, n_max, p->tol, p->sweeps, p->d_ctl, st, p->jac_cfg,
                                       p->lead, p->jac_spin));
-        CUDA_TRY(launch_truncate<float>(p->d_desc, ng, st));
+        CUDA_TRY(launch_truncate<float>(p->d_desc, ng, n_max, st));
         CUDA_TRY(launch_left<float>(p->d_desc, ng, m_max, p->k_max, st));
         CUDA_TRY(launch_right<float>(p->d_desc, ng, p->k_max, n_max, st));
         if (p->canon) CUDA_TRY(launch_left_canon<float>(p->d_desc, ng, m_max, p->k_max, st));

@@ -114,8 +114,9 @@ template <typename T>
 cudaError_t launch_jacobi(const GateDesc* d, int n_gates, int m_max, int n_max, double tol,
                           int max_sweeps, JacobiCtl* ctl, cudaStream_t s, int cfg = 0, int n_lead = 0,
                           unsigned spin_limit = 0);
+// n_max: the largest 2 chi_R of the batch (grid of the column-norm pass)
 template <typename T>
-cudaError_t launch_truncate(const GateDesc* d, int n_gates, cudaStream_t s);
+cudaError_t launch_truncate(const GateDesc* d, int n_gates, int n_max, cudaStream_t s);
 template <typename T>
 cudaError_t launch_left(const GateDesc* d, int n_gates, int m_max, int k_max, cudaStream_t s);
 template <typename T>

@@ -143,7 +143,7 @@ extern "C" tnsim_status tnsim_two_site_update_noalloc(
     const GateDesc* dd = (const GateDesc*)(base + OFF_DESC);
     NA_TRY(launch_theta<float>(dd, 1, chi_l, chi_r, st));
     NA_TRY(launch_jacobi<float>(dd, 1, 2 * chi_l, 2 * chi_r, 0.0, 40, (JacobiCtl*)(base + OFF_CTL), st));
-    NA_TRY(launch_truncate<float>(dd, 1, st));
+    NA_TRY(launch_truncate<float>(dd, 1, 2 * chi_r, st));
     NA_TRY(launch_left<float>(dd, 1, 2 * chi_l, kcap, st));
     NA_TRY(launch_right<float>(dd, 1, kcap, 2 * chi_r, st));
     GateOut o;

@@ -675,3 +675,52 @@ def test_full_size_chi256_layer_sampled_gates(T, cfg, gemm):
         blk_gpu = np.einsum("lxb,byr->lxyr", after[q], after[q + 1])
         assert np.linalg.norm(blk_gpu - blk_ref) / np.linalg.norm(blk_ref) <= 1e-4
     m.close()
+
+
+@pytest.fixture(scope="module")
+def chi256_state(T):
+    """A saturated 100-qubit chi 256 Haar brickwork state (11 layers, complex64) and
+    the next layer."""
+    n, chi = 100, 256
+    circ = W.brickwork_su4(n, 12, seed=9)
+    m = T.MPS(n, dtype=T.TNSIM_C64, chi_max=chi)
+    for lay in circ.layers[:11]:
+        m.apply_layer(lay)
+    assert int(np.max(m.bond_dims())) == chi
+    sites = m.export_sites()
+    m.close()
+    return sites, circ.layers[11]
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("mode,bound", [("FP32", 1e-6), ("FP32_3M", 5e-6), ("TF32X3", 1e-5), ("BF16X3", 1e-5)])
+def test_c3_precision_modes_chi256(T, chi256_state, mode, bound):
+    """The precision workload's per-result error at chi 256 (the gate-set circuit of C3
+    never entangles beyond bond 16, so chi 256 comes from the Haar brickwork): every
+    contraction arithmetic applies the same layer to the same saturated state, in the
+    benchmark's launch configuration, and for 8 sampled gates the kept singular values
+    are held to a per-mode bound (of s_max) against the oracle applied to the same
+    input sites, the discarded weight to 1e-5, and the gauge-invariant two-site block
+    to 1 - F <= 1e-6."""
+    sites, lay = chi256_state
+    n, chi = 100, 256
+    m = T.MPS(n, dtype=T.TNSIM_C64, chi_max=chi, gemm=getattr(T, "TNSIM_GEMM_" + mode))
+    T.tnsim_set_jacobi_config(m.h, 2)
+    m.import_sites(sites)
+    eps = m.apply_layer(lay)
+    after = m.export_sites()
+    worst = 0.0
+    for i in np.linspace(0, len(lay.pairs) - 1, 8).astype(int):
+        q = int(lay.pairs[i])
+        mm = om.MPS([sites[q], sites[q + 1]])
+        rec = om.apply_2q(mm, 0, lay.g4[i], chi)
+        s_gpu = m.spectrum(q + 1)
+        assert len(s_gpu) == rec.k
+        worst = max(worst, float(np.max(np.abs(s_gpu - rec.s_kept)) / rec.s_kept[0]))
+        assert abs(eps[i] - rec.eps) <= 1e-5
+        blk_ref = np.einsum("lxb,byr->lxyr", mm.sites[0], mm.sites[1])
+        blk_gpu = np.einsum("lxb,byr->lxyr", after[q], after[q + 1])
+        f = abs(np.vdot(blk_ref, blk_gpu)) ** 2 / (np.vdot(blk_ref, blk_ref).real * np.vdot(blk_gpu, blk_gpu).real)
+        assert 1 - f <= 1e-6, (mode, q, 1 - f)
+    assert worst <= bound, (mode, worst)
+    m.close()
