@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(256) k_theta(const GateDesc* __restrict__ gd) 
 
     C* Wm = (C*)d.W;
     C* T0 = (C*)d.theta0;
-    double fro = 0.0;
+    SqAcc<T> fsq;  // |theta|_F^2 of this thread's elements
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
         const int l = l0 + tx + 16 * i;
@@ -155,12 +155,14 @@ __global__ void __launch_bounds__(256) k_theta(const GateDesc* __restrict__ gd) 
                         const size_t idx = (size_t)(bb * chiR + r) * m + 2 * l + aa;
                         Wm[idx] = t;
                         T0[idx] = t;
-                        fro += (double)t.x * (double)t.x + (double)t.y * (double)t.y;
+                        fsq.add(t.x);
+                        fsq.add(t.y);
                     }
                 }
             }
         }
     }
+    double fro = fsq.value();
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) fro += __shfl_xor_sync(0xffffffffu, fro, o);
     if ((tid & 31) == 0 && fro != 0.0) atomicAdd(&d.out->frob2, fro);
@@ -380,7 +382,7 @@ __global__ void __launch_bounds__(256) k_theta_3m(const GateDesc* __restrict__ g
     }
     C* Wm = (C*)d.W;
     C* T0 = (C*)d.theta0;
-    double fro = 0.0;
+    SqAcc<float> fsq;  // |theta|_F^2 of this thread's elements
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
         const int l = l0 + tx + 16 * i;
@@ -408,12 +410,14 @@ __global__ void __launch_bounds__(256) k_theta_3m(const GateDesc* __restrict__ g
                         const size_t idx = (size_t)(bb * chiR + r) * m + 2 * l + aa;
                         Wm[idx] = t;
                         T0[idx] = t;
-                        fro += (double)t.x * (double)t.x + (double)t.y * (double)t.y;
+                        fsq.add(t.x);
+                        fsq.add(t.y);
                     }
                 }
             }
         }
     }
+    double fro = fsq.value();
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) fro += __shfl_xor_sync(0xffffffffu, fro, o);
     if ((tid & 31) == 0 && fro != 0.0) atomicAdd(&d.out->frob2, fro);

@@ -34,8 +34,7 @@
 namespace tnsim {
 
 constexpr int TC_M = 128;          // output tile rows (64 l x 2 p0)
-constexpr int TC_RH = 32;          // r values per tile (two halves: p1 = 0, 1)
-constexpr int TC_STAGES = 2;       // shared-memory stages: the TMA of stage k+1 overlaps the MMAs of stage k
+constexpr int TC_RH = 64;          // r values per tile (two halves: p1 = 0, 1)
 constexpr int TC_N = 2 * TC_RH;    // output tile columns
 constexpr int TC_THREADS = 128;
 constexpr unsigned kTcSpin = 1u << 26;     // default polls of a bounded mbarrier wait (about a second)
@@ -208,9 +207,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_theta_tc(const GateDesc* __re
     constexpr int KS = PlaneT<MODE>::KS;                    // K per stage (128 bytes)
     constexpr int KMMA = (MODE == 0) ? 8 : 16;               // K per MMA instruction
     constexpr uint32_t FMT = (MODE == 0) ? 2u : 1u;          // TF32 / BF16
-    constexpr uint32_t TILE_A = TC_M * 128;                  // bytes of one A plane tile (128 rows x 128 B)
-    constexpr uint32_t TILE_B = 2 * TC_RH * 128;             // bytes of one B plane tile (both p1 halves)
-    constexpr uint32_t STAGE_BYTES = 4 * TILE_A + 4 * TILE_B;  // one K stage: eight plane tiles
+    constexpr uint32_t TILE = TC_M * 128;                    // bytes of one 128-row plane tile
     const GateDesc& d = gd[blockIdx.z];
     const int q = d.q;
     const int chiL = d.chi[q], chiM = d.chi[q + 1], chiR = d.chi[q + 2];
@@ -220,9 +217,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_theta_tc(const GateDesc* __re
     const int kuse = (chiM + KS - 1) / KS * KS;
 
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    // 1024-byte aligned, per stage: 4 A plane tiles (16 KB each), then 4 B plane tiles (8 KB each)
+    // 1024-byte aligned: 4 A plane tiles then 4 B plane tiles (each 16 KB)
     unsigned char* tiles = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    __shared__ __align__(8) uint64_t bar_full[TC_STAGES], bar_mma[TC_STAGES];
+    __shared__ __align__(8) uint64_t bar_full, bar_mma;
     __shared__ uint32_t tmem_base;
     __shared__ int s_fail;
     __shared__ float2 Gs[16];
@@ -248,10 +245,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_theta_tc(const GateDesc* __re
         Gs[tid] = make_float2((float)re, (float)im);
     }
     if (tid == 0) {
-        for (int st = 0; st < TC_STAGES; ++st) {
-            mbar_init(smem_u32(&bar_full[st]), 1);
-            mbar_init(smem_u32(&bar_mma[st]), 1);
-        }
+        mbar_init(smem_u32(&bar_full), 1);
+        mbar_init(smem_u32(&bar_mma), 1);
         s_fail = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -271,50 +266,34 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_theta_tc(const GateDesc* __re
     const uint32_t sbase = smem_u32(tiles);
     const int nk = kuse / KS;
     const unsigned lim = d.wait_polls > 0 ? (unsigned)d.wait_polls : kTcSpin;
-    // One thread issues every copy and every MMA and is the only one waiting on the
-    // mbarriers; the others meet it at the barrier after the K loop.  Each stage's two
-    // barriers alternate between one arrival and one wait, so a barrier is never more
-    // than one phase ahead of its waiter.
-    if (tid == 0) {
-        int issued_full[TC_STAGES] = {0, 0}, waited_full[TC_STAGES] = {0, 0};
-        int issued_mma[TC_STAGES] = {0, 0}, waited_mma[TC_STAGES] = {0, 0};
-        auto load_stage = [&](int kb) {
-            const int st = kb & 1;
-            const uint32_t a0 = sbase + st * STAGE_BYTES, b0 = a0 + 4 * TILE_A;
-            const uint32_t bar = smem_u32(&bar_full[st]);
-            mbar_expect_tx(bar, STAGE_BYTES);
-            for (int p = 0; p < 4; ++p) tma_load_3d(a0 + p * TILE_A, mapA, kb * KS, m0, zA + p, bar);
+    uint32_t pend_bar = 0, pend_phase = 0;   // the barrier phase left pending by a timeout
+    for (int kb = 0; kb < nk; ++kb) {
+        if (tid == 0 && !s_fail) {
+            mbar_expect_tx(smem_u32(&bar_full), 8 * TILE);
+            for (int p = 0; p < 4; ++p) tma_load_3d(sbase + p * TILE, mapA, kb * KS, m0, zA + p, smem_u32(&bar_full));
             for (int p = 0; p < 4; ++p) {
-                tma_load_3d(b0 + p * TILE_B, mapB, kb * KS, r0, zB + p, bar);
-                tma_load_3d(b0 + p * TILE_B + TILE_B / 2, mapB, kb * KS, chiR + r0, zB + p, bar);
+                tma_load_3d(sbase + (4 + p) * TILE, mapB, kb * KS, r0, zB + p, smem_u32(&bar_full));
+                tma_load_3d(sbase + (4 + p) * TILE + TILE / 2, mapB, kb * KS, chiR + r0, zB + p, smem_u32(&bar_full));
             }
-            ++issued_full[st];
-        };
-        bool ok = true;
-        load_stage(0);
-        for (int kb = 0; kb < nk && ok; ++kb) {
-            const int st = kb & 1;
-            if (kb + 1 < nk) {
-                const int sn = (kb + 1) & 1;
-                // the stage the next copy overwrites was last read by the MMAs of kb - 1
-                if (issued_mma[sn] > waited_mma[sn]) {
-                    if (!mbar_wait(smem_u32(&bar_mma[sn]), waited_mma[sn] & 1, lim)) { ok = false; break; }
-                    ++waited_mma[sn];
-                }
-                load_stage(kb + 1);
-            }
-            if (!mbar_wait(smem_u32(&bar_full[st]), waited_full[st] & 1, lim)) { ok = false; break; }
-            ++waited_full[st];
+        }
+        if (!mbar_wait(smem_u32(&bar_full), kb & 1, lim)) atomicExch(&s_fail, 1);
+        __syncthreads();
+        if (s_fail) {
+            // the copies of this stage may still be in flight (no MMA of it was issued)
+            pend_bar = smem_u32(&bar_full);
+            pend_phase = kb & 1;
+            break;
+        }
+        if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            // plane tiles: A_re_hi, A_re_lo, A_im_hi, A_im_lo, then B_re_hi, B_re_lo, B_im_hi, B_im_lo
-            const uint32_t a0 = sbase + st * STAGE_BYTES, b0 = a0 + 4 * TILE_A;
+            // plane tiles: 0 A_re_hi, 1 A_re_lo, 2 A_im_hi, 3 A_im_lo, 4 B_re_hi, 5 B_re_lo, 6 B_im_hi, 7 B_im_lo
             const uint32_t idp = inst_desc(FMT, 0), idn = inst_desc(FMT, 1);
             for (int j = 0; j < KS / KMMA; ++j) {
                 const uint32_t off = j * KMMA * (MODE == 0 ? 4 : 2);
                 uint64_t a[4], b[4];
                 for (int p = 0; p < 4; ++p) {
-                    a[p] = smem_desc(a0 + p * TILE_A + off);
-                    b[p] = smem_desc(b0 + p * TILE_B + off);
+                    a[p] = smem_desc(sbase + p * TILE + off);
+                    b[p] = smem_desc(sbase + (4 + p) * TILE + off);
                 }
                 const uint32_t acc0 = (kb > 0 || j > 0) ? 1u : 0u;
                 // Re += Ar Br - Ai Bi  (hi.hi + hi.lo + lo.hi)
@@ -333,36 +312,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_theta_tc(const GateDesc* __re
                 mma<MODE>(t_im, a[3], b[0], idp, 1u);
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             smem_u32(&bar_mma[st]))
+                             smem_u32(&bar_mma))
                          : "memory");
-            ++issued_mma[st];
         }
-        // the accumulators are complete when the last commit has arrived (a commit tracks
-        // every earlier MMA of this thread)
-        if (ok) {
-            const int st = (nk - 1) & 1;
-            if (issued_mma[st] > waited_mma[st]) {
-                if (!mbar_wait(smem_u32(&bar_mma[st]), waited_mma[st] & 1, lim)) ok = false;
-                else ++waited_mma[st];
-            }
-        }
-        if (!ok) {
-            // drain with the default limit: every copy and every MMA issued has landed
-            // before the CTA releases its shared memory and TMEM
-            for (int st = 0; st < TC_STAGES; ++st) {
-                while (waited_full[st] < issued_full[st]) {
-                    mbar_wait(smem_u32(&bar_full[st]), waited_full[st] & 1, kTcSpin);
-                    ++waited_full[st];
-                }
-                while (waited_mma[st] < issued_mma[st]) {
-                    mbar_wait(smem_u32(&bar_mma[st]), waited_mma[st] & 1, kTcSpin);
-                    ++waited_mma[st];
-                }
-            }
-            s_fail = 1;
+        // the stage buffers are reused by the next TMA only after the MMAs read them
+        if (!mbar_wait(smem_u32(&bar_mma), kb & 1, lim)) atomicExch(&s_fail, 1);
+        __syncthreads();
+        if (s_fail) {
+            // this stage's copies have landed; its MMAs may still be running
+            pend_bar = smem_u32(&bar_mma);
+            pend_phase = kb & 1;
+            break;
         }
     }
-    __syncthreads();
+    if (s_fail && tid == 0) mbar_wait(pend_bar, pend_phase, kTcSpin);   // drain before TMEM and smem go
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
     if (!s_fail) {
@@ -373,7 +336,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_theta_tc(const GateDesc* __re
         const int row = m0 + i_t;          // (l, c) = (row / 2, row % 2)
         const int c = row & 1;
         const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
-        double fro = 0.0;
+        SqAcc<float> fsq;  // |theta|_F^2 of this thread's elements
         for (int rc = 0; rc < TC_RH; rc += 16) {
             float re0[16], im0[16], re1[16], im1[16];
             tmem_ld16(t_re + lane_off + rc, re0);
@@ -406,11 +369,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_theta_tc(const GateDesc* __re
                         const size_t idx = (size_t)(bb * chiR + r) * m + row;
                         Wm[idx] = t;
                         T0[idx] = t;
-                        fro += (double)t.x * t.x + (double)t.y * t.y;
+                        fsq.add(t.x);
+                        fsq.add(t.y);
                     }
                 }
             }
         }
+        double fro = fsq.value();
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) fro += __shfl_xor_sync(0xffffffffu, fro, o);
         if (lane == 0 && fro != 0.0) atomicAdd(&d.out->frob2, fro);
@@ -431,7 +396,7 @@ static cudaError_t launch_tc(const GateDesc* d, int n_gates, int chiL_max, int c
     k_split<MODE><<<gs, 256, 0, s>>>(d);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const size_t smem = (size_t)TC_STAGES * (4 * TC_M * 128 + 4 * 2 * TC_RH * 128) + 1024;
+    const size_t smem = 8 * TC_M * 128 + 1024;
     e = cudaFuncSetAttribute(k_theta_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((2 * chiL_max + TC_M - 1) / TC_M, (chiR_max + TC_RH - 1) / TC_RH, n_gates);

@@ -32,9 +32,10 @@ __device__ __forceinline__ bool after(double ka, int ia, double kb, int ib) {
     return ka < kb || (ka == kb && ia > ib);
 }
 
-// Squared column norms of the converged W in FP64, spread over many CTAs: grid
-// (column chunks of 32, gates), one warp per column at a time, 16-byte loads.  The
-// unsorted values go to d.s2 (k_truncate sorts them in place).
+// Squared column norms of the converged W, spread over many CTAs: grid (column chunks
+// of 32, gates), one warp per column at a time, 16-byte loads, per-lane SqAcc sums
+// (double-length FP32 for complex64), then an FP64 warp reduction.  The unsorted
+// values go to d.s2 (k_truncate sorts them in place).
 template <typename T>
 __global__ void __launch_bounds__(256) k_colnorm2(const GateDesc* __restrict__ gd) {
     using C = typename CT<T>::type;
@@ -49,16 +50,21 @@ __global__ void __launch_bounds__(256) k_colnorm2(const GateDesc* __restrict__ g
     const int units = m / PER;
     for (int col = c0 + warp; col < min(c0 + CN_COLS, n); col += 8) {
         const C* wc = (const C*)d.W + (size_t)col * m;
-        double acc = 0.0;
+        SqAcc<T> sq;
         for (int u = lane; u < units; u += 32) {
             if constexpr (sizeof(C) == 8) {
                 const float4 v = __ldcg(reinterpret_cast<const float4*>(wc) + u);
-                acc += (double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z + (double)v.w * v.w;
+                sq.add(v.x);
+                sq.add(v.y);
+                sq.add(v.z);
+                sq.add(v.w);
             } else {
                 const double2 z = __ldcg(reinterpret_cast<const double2*>(wc) + u);
-                acc = fma(z.x, z.x, fma(z.y, z.y, acc));
+                sq.add(z.x);
+                sq.add(z.y);
             }
         }
+        double acc = sq.value();
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if (lane == 0) d.s2[col] = acc;
@@ -233,16 +239,25 @@ __global__ void __launch_bounds__(256) k_left(const GateDesc* __restrict__ gd) {
     const int row0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
     if (row0 >= m || j0 >= k) return;
     __shared__ C tile[32][33];
+    __shared__ T inv_s[32];
+    __shared__ int col_s[32];
     const C* Wm = (const C*)d.W;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
+    if (threadIdx.x < 32) {
+        // 1 / s_j and the column of each kept j of this tile, once per CTA (FP64 runs at
+        // 1/64 of the FP32 rate: not per element)
+        const int j = j0 + threadIdx.x;
+        const double s2j = j < k ? d.s2[j] : 0.0;
+        inv_s[threadIdx.x] = s2j > 0.0 ? (T)(1.0 / sqrt(s2j)) : (T)0;
+        col_s[threadIdx.x] = j < k ? d.perm[j] : 0;
+    }
+    __syncthreads();
     for (int jj = ty; jj < 32; jj += 8) {
         const int j = j0 + jj;
         C v; v.x = 0; v.y = 0;
         if (j < k && row0 + tx < m) {
-            const int col = d.perm[j];
-            const double s2j = d.s2[j];
-            const T inv = s2j > 0.0 ? (T)(1.0 / sqrt(s2j)) : (T)0;
-            v = Wm[(size_t)col * m + row0 + tx];
+            const T inv = inv_s[jj];
+            v = Wm[(size_t)col_s[jj] * m + row0 + tx];
             v.x *= inv; v.y *= inv;
         }
         tile[jj][tx] = v;

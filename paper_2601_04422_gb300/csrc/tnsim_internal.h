@@ -82,6 +82,34 @@ struct GateDesc {
     int wait_polls;
 };
 
+#ifdef __CUDACC__
+// x^2 added to the double-length sum (s, c) with FP32 operations only: the product is
+// split exactly (p + e = x^2 with e = fma(x, x, -p)) and p enters by Knuth's TwoSum, so
+// s + c carries the sum to about eps^2 relative.  GB300 runs FP64 at 1/64 of the FP32
+// rate; per-element FP64 arithmetic bounded the passes that accumulate norms.
+__device__ __forceinline__ void add_sq(float x, float& s, float& c) {
+    const float p = x * x;
+    const float e = fmaf(x, x, -p);
+    const float t = s + p;
+    const float z = t - s;
+    c += (s - (t - z)) + (p - z) + e;
+    s = t;
+}
+// Sum of squares per thread: double-length FP32 for complex64, FP64 for complex128;
+// value() is the FP64 result that the warp and block reductions combine.
+template <typename T> struct SqAcc;
+template <> struct SqAcc<float> {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x) { add_sq(x, s, c); }
+    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+template <> struct SqAcc<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double x) { s = fma(x, x, s); }
+    __device__ __forceinline__ double value() const { return s; }
+};
+#endif
+
 // largest m of a QR-preconditioned gate (its panel of columns sits in shared memory)
 constexpr int kQrMaxRows = 1536;
 #ifdef __CUDACC__
