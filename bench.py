@@ -255,10 +255,10 @@ def infidelity(sa, sb) -> float:
 
 def kernels_per_layer(gemm: str, cfg: int) -> int:
     """Kernels one batched layer launches: contraction (split + tcgen05 GEMM on the tensor
-    path), QR (configurations 2, 3), Jacobi, truncation, left site, right site, and the two
-    site kernels of the QR route."""
+    path), QR (configurations 2, 3), Jacobi, truncation (column norms + selection), left
+    site, right site, and the two site kernels of the QR route."""
     theta = 2 if gemm in ("tf32x3", "bf16x3") else 1
-    return theta + 1 + 1 + 1 + 1 + (3 if cfg & 2 else 0)
+    return theta + 1 + 2 + 1 + 1 + (3 if cfg & 2 else 0)
 
 
 def run_reference(args, world, rank):
