@@ -40,6 +40,23 @@ def test_every_configuration_exact_complex128(T, cfg):
 
 
 @pytest.mark.parametrize("cfg", [0, 1, 2, 3])
+def test_every_configuration_exact_complex128_wide_blocks(T, cfg):
+    """14 qubits without truncation (bonds up to 128, gated blocks up to 256 rows,
+    several column blocks per gate in every configuration): the dense state vector
+    within 1e-10."""
+    n = 14
+    circ = W.brickwork_su4(n, 12, seed=8)
+    m = T.MPS(n, dtype=T.TNSIM_C128, chi_max=128)
+    T.tnsim_set_jacobi_config(m.h, cfg)
+    m.run(circ)
+    assert max(m.bond_dims()) == 128
+    psi = dense.run_circuit(circ)
+    amps = m.amplitudes(_all_bits(n))
+    assert np.linalg.norm(amps - psi) / np.linalg.norm(psi) < 1e-10
+    m.close()
+
+
+@pytest.mark.parametrize("cfg", [0, 1, 2, 3])
 def test_every_configuration_complex64_per_layer(T, cfg):
     """24 qubits, chi 64 (m up to 128): every layer against the oracle on the same input."""
     circ = W.brickwork_u2_su4(24, 9, seed=6)
@@ -64,7 +81,7 @@ def test_autotune_keeps_the_state_and_picks_a_configuration(T):
     dims = list(m.bond_dims())
     lay = circ.layers[8]
     choice, ms = T.tnsim_autotune(m.h, lay.pairs, lay.g4, reps=2)
-    assert choice in range(T.TNSIM_JACOBI_CONFIGS) and len(ms) == 4 and np.all(ms > 0) and ms[choice] == ms.min()
+    assert choice in range(T.TNSIM_JACOBI_CONFIGS) and len(ms) == T.TNSIM_JACOBI_CONFIGS and np.all(ms > 0) and ms[choice] == ms.min()
     assert list(m.bond_dims()) == dims
     for a, b in zip(m.export_sites(), before):
         assert np.array_equal(a, b)
@@ -75,5 +92,5 @@ def test_autotune_keeps_the_state_and_picks_a_configuration(T):
         sg = m.spectrum(r.q + 1)
         assert len(sg) == r.k and np.max(np.abs(sg - r.s_kept)) / r.s_kept[0] <= 1e-5
     with pytest.raises(T.TnsimError):
-        T.tnsim_set_jacobi_config(m.h, 4)
+        T.tnsim_set_jacobi_config(m.h, T.TNSIM_JACOBI_CONFIGS)
     m.close()
