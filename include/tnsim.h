@@ -268,9 +268,13 @@ tnsim_status tnsim_sample(tnsim_mps* m, int64_t n_shots, const double* uniforms,
  * gated block is square (2 chi_L == 2 chi_R <= 1536) in the paper's form: theta = Q R
  * by blocked Householder reflections, the Jacobi iteration runs on the columns of
  * R^H (fewer sweeps), the left site is theta V S^-1 and the right site S V^H is read
- * off the converged columns; Q is never formed.  Same kept spectrum and state up to
- * the Jacobi tolerance. */
-#define TNSIM_JACOBI_CONFIGS 4
+ * off the converged columns; Q is never formed.  Bit 2 (complex64 states): every
+ * visit forms the block pair's Gram matrix X^H X on the tensor cores, applies the
+ * visit's rotations to it (same order and parameters as the column rotations) while
+ * accumulating the rotation V, and updates the columns as X V on the tensor cores
+ * (3xTF32); bit 0 then has no effect, and complex128 states run bits 0-1 only.  Same
+ * kept spectrum and state up to the Jacobi tolerance in every configuration. */
+#define TNSIM_JACOBI_CONFIGS 8
 
 /* Use Jacobi configuration cfg (0 .. TNSIM_JACOBI_CONFIGS - 1) for the later
  * launches of m.  Errors: EINVAL. */

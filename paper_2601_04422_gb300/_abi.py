@@ -342,7 +342,7 @@ def tnsim_sample(h, uniforms):
     return bits, nodes.value
 
 
-TNSIM_JACOBI_CONFIGS = 4
+TNSIM_JACOBI_CONFIGS = 8
 
 
 def tnsim_set_jacobi_config(h, cfg: int):

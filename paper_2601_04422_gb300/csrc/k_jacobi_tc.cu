@@ -1,0 +1,542 @@
+// Complex64 one-sided Jacobi SVD whose visits rotate the block pair's Gram matrix and
+// apply the accumulated rotation to the columns with tcgen05 tensor-core products.
+//
+// The schedule is k_jacobi.cu's: columns in blocks of BC = 16, every block pair visited
+// once per sweep in round-robin order, a visit rotating the 16 x 16 cross pairs in 16
+// steps of 16 disjoint pairs (and, in round 0, the pairs inside each block), a
+// persistent launch claiming visits from the per-gate claim words.  What a visit of the
+// blocks I, J (X = [X_I X_J], m x 32 columns of W) computes is the same sequence of
+// Jacobi rotations (Sec. IV.A; Hestenes), with the inner products taken from the Gram
+// matrix instead of the columns:
+//   1. G = X^H X on the tensor cores: with Y = [Re X | Im X] (m x 64 real), the product
+//      Y^T Y in 3xTF32 (hi.hi + hi.lo + lo.hi, FP32 accumulation in TMEM) over K tiles of
+//      32 rows; Re G = P11 + P22, Im G = P12 - P21.
+//   2. The visit's rotations on G: a pair (i, j) takes a = G_ii, b = G_jj, g = G_ij and
+//      the rotation parameters of k_jacobi; a step's rotations J (16 disjoint pairs) give
+//      G <- J^H G J and D <- D J + (J - I), D = V - I the accumulated rotation minus the
+//      identity.  Every new entry is its old value plus a correction summed first (the
+//      single-rounding update of k_jacobi); the rotated pair's norms become a - t|g| and
+//      b + t|g| and its coupling 0, as for the tracked norms there.
+//   3. X <- X + X D on the tensor cores: [Re X | Im X] . [[Re D, Im D], [-Im D, Re D]]
+//      in 3xTF32, chunks of 128 rows, the correction added to X in the epilogue (so a
+//      column that barely moves keeps its bits).  A visit that rotates nothing writes
+//      nothing back.
+// Each visit reads its columns twice (once for G, once for the update) and writes them
+// once; the rotation steps touch only the 32 x 32 matrices in shared memory.
+//
+// Operand tiles are written by the threads into 128-byte-swizzled K-major layout (the
+// layout a SWIZZLE_128B TMA copy produces), made visible to the tensor cores with a
+// proxy fence, and consumed by MMAs one thread issues; completion is signalled by
+// tcgen05.commit on an mbarrier whose wait is bounded (GateDesc::wait_polls, default
+// 2^26 polls).  A wait that runs out waits once more (bounded) for the MMAs in flight,
+// sets the launch's error flag and the gate's status 5, and the CTA leaves after
+// releasing its TMEM; every other CTA leaves at its next claim.
+#include <float.h>
+
+#include "jacobi_sched.cuh"
+#include "tc_common.cuh"
+#include "tnsim_internal.h"
+
+namespace tnsim {
+
+namespace {
+
+constexpr int GB = 16;                 // columns per block
+constexpr int GC = 2 * GB;             // complex columns of a visit
+constexpr int GT = 512;                // threads of a CTA
+constexpr int GS = GC + 1;             // row stride of the 32 x 32 matrices in shared memory
+constexpr unsigned kGramSpin = 1u << 26;
+
+// dynamic shared memory (1024-byte aligned base)
+constexpr uint32_t TILE128 = 128 * 128;                 // 128 rows x 128 bytes
+constexpr uint32_t TILE64 = 64 * 128;                   // 64 rows x 128 bytes
+constexpr uint32_t OFF_A = 0;                           // 4 x TILE128: Gram K-tiles / update A tiles
+constexpr uint32_t OFF_P = 4 * TILE128;                 // 64 x 65 floats: Y^T Y read back from TMEM
+constexpr uint32_t OFF_B = OFF_P + 64 * 65 * 4 + 256;   // 4 x TILE64: update B tiles (1024-aligned below)
+constexpr uint32_t OFF_B_AL = (OFF_B + 1023) / 1024 * 1024;
+constexpr uint32_t OFF_G = OFF_B_AL + 4 * TILE64;       // 2 x 32 x 33 float2
+constexpr uint32_t OFF_D = OFF_G + 2 * GC * GS * 8;     // 2 x 32 x 33 float2
+constexpr uint32_t SMEM_USED = OFF_D + 2 * GC * GS * 8;
+constexpr uint32_t SMEM_BYTES = SMEM_USED + 1024;       // slack for aligning the base
+
+struct PairPrm {
+    float cm1, sr, si, tg;
+    int rot;
+};
+
+// Partner of index p (0..31) in a step.  Cross step sft: column w of block I meets
+// column (w + sft) mod 16 of block J.  Intra step t: the circle-method pair of round t
+// among the 16 columns of each block (rr_pair(16, t, .)); its inverse: 15 <-> t, and
+// x <-> (2t - x) mod 15 otherwise.
+__device__ __forceinline__ int partner_of(int p, int step, bool intra) {
+    if (!intra) return p < GB ? GB + (p + step) % GB : (p - GB - step + 2 * GB) % GB;
+    const int base = p < GB ? 0 : GB, x = p - base;
+    const int y = x == GB - 1 ? step : (x == step ? GB - 1 : (2 * step - x + 2 * (GB - 1)) % (GB - 1));
+    return base + y;
+}
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+// a * b
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+// conj(a) * b
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.x, b.y, -a.y * b.x));
+}
+
+// The rotation factors of index x in the current step: J_xx = 1 + cm1 and the
+// off-diagonal entry J_{x' x} of its column (x' its partner): -conj(s e) if x is the
+// pair's first index, s e if it is the second.  Zero when the pair does not rotate.
+struct Fac {
+    float cm1;
+    float2 off;
+    int rot, first, part;
+    float tg;
+};
+__device__ __forceinline__ Fac fac_of(const PairPrm* prm, int x, int step, bool intra) {
+    Fac f;
+    f.part = partner_of(x, step, intra);
+    f.first = x < f.part;
+    const PairPrm& q = prm[f.first ? x : f.part];
+    f.rot = q.rot;
+    f.cm1 = q.rot ? q.cm1 : 0.f;
+    f.tg = q.tg;
+    f.off = q.rot ? (f.first ? make_float2(-q.sr, q.si) : make_float2(q.sr, q.si)) : make_float2(0.f, 0.f);
+    return f;
+}
+
+__device__ __forceinline__ void st_split(unsigned char* hi_tile, unsigned char* lo_tile, uint32_t off, float v) {
+    const float h = tf32_round(v);
+    *reinterpret_cast<float*>(hi_tile + off) = h;
+    *reinterpret_cast<float*>(lo_tile + off) = tf32_round(v - h);
+}
+
+// local column c (0..31) of a visit -> column of W, or -1 past the end of a block
+__device__ __forceinline__ int vcol(int c, int colI, int nI, int colJ, int nJ) {
+    return c < GB ? (c < nI ? colI + c : -1) : (c - GB < nJ ? colJ + c - GB : -1);
+}
+
+// issue (one thread) the 3xTF32 products of one 32-wide K tile: D += Ahi Bhi + Ahi Blo + Alo Bhi
+__device__ __forceinline__ void mma_ktile(uint32_t d_tmem, uint32_t a_hi, uint32_t a_lo, uint32_t b_hi,
+                                          uint32_t b_lo, uint32_t idesc, bool first) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const uint64_t ah = smem_desc(a_hi + 32 * j), al = smem_desc(a_lo + 32 * j);
+        const uint64_t bh = smem_desc(b_hi + 32 * j), bl = smem_desc(b_lo + 32 * j);
+        mma_tf32(d_tmem, ah, bh, idesc, (first && j == 0) ? 0u : 1u);
+        mma_tf32(d_tmem, ah, bl, idesc, 1u);
+        mma_tf32(d_tmem, al, bh, idesc, 1u);
+    }
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+}  // namespace
+
+// Persistent kernel (protocol of k_jacobi: claim a visit, process it, report it; the
+// last report of a round opens the gate's next round or ends its iteration).
+__global__ void __launch_bounds__(GT, 1)
+k_jacobi_tc(const GateDesc* __restrict__ gd, int n_gates, int n_lead, double tol_in, int max_sweeps,
+            JacobiCtl* __restrict__ ctl, unsigned spin_limit) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* sm = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    float* Ps = reinterpret_cast<float*>(sm + OFF_P);
+    float2* Gb = reinterpret_cast<float2*>(sm + OFF_G);   // two buffers of GC x GS
+    float2* Db = reinterpret_cast<float2*>(sm + OFF_D);
+    const uint32_t sbase = smem_u32(sm);
+    __shared__ int s_g, s_rnd, s_v, s_exit, s_rot, s_vis, s_fail, s_ok;
+    // per step (double-buffered by the step's parity: warp 0 may write a step's entries
+    // while slower warps still read the previous step's, never two steps ahead)
+    __shared__ int s_any[2];
+    __shared__ PairPrm s_prm[2][GC];
+    __shared__ short s_V[kScanTable];
+    __shared__ __align__(8) uint64_t s_bar[2];
+    __shared__ uint32_t s_tmem;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    unsigned spins = 0, last_progress = 0;
+    int scan0 = (int)(((long long)blockIdx.x * n_lead) / gridDim.x);
+    for (int g = tid; g < n_gates && g < kScanTable; g += blockDim.x) s_V[g] = (short)tour_of<GB>(gd[g]).V;
+    if (tid == 0) {
+        mbar_init(smem_u32(&s_bar[0]), 1);
+        mbar_init(smem_u32(&s_bar[1]), 1);
+        s_fail = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                     "r"(128));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t t_gram = s_tmem, t_upd = s_tmem + 64;
+    const uint32_t idesc = idesc_mn(2u, 0u, 128, 64);
+    uint32_t ph[2] = {0u, 0u};         // parity of the next completion of each barrier
+    bool pend[2] = {false, false};     // a commit on the barrier not yet waited for
+    const uint32_t bar0 = smem_u32(&s_bar[0]), bar1 = smem_u32(&s_bar[1]);
+
+    // (thread 0) bounded wait for the outstanding commit on barrier b; false on timeout
+    auto wait_bar = [&](int b, unsigned lim) -> bool {
+        if (!pend[b]) return true;
+        const bool ok = mbar_wait(b ? bar1 : bar0, ph[b], lim);
+        if (ok) {
+            ph[b] ^= 1u;
+            pend[b] = false;
+        }
+        return ok;
+    };
+
+    for (;;) {
+        if (warp == 0) {
+            int found = 0, fg = -1, frnd = 0, fv = 0, err = 0;
+            if (lane == 0) err = *((volatile int*)&ctl->error) | s_fail;
+            err = __shfl_sync(0xffffffffu, err, 0);
+            if (!err) claim_scan<GB>(gd, n_gates, s_V, scan0, lane, found, fg, frnd, fv);
+            if (found) scan0 = fg;
+            if (lane == 0) {
+                s_exit = 0;
+                s_g = found ? fg : -1;
+                s_rnd = frnd;
+                s_v = fv;
+                if (err || (!found && (*((volatile int*)&ctl->n_finished) >= n_gates ||
+                                       *((volatile int*)&ctl->error))))
+                    s_exit = 1;
+                s_rot = 0;
+                s_vis = 0;
+            }
+        }
+        __syncthreads();
+        if (s_exit) break;
+        if (s_g < 0) {
+            if (tid == 0) {
+                const unsigned p = *((volatile unsigned*)&ctl->progress);
+                if (p != last_progress) {
+                    last_progress = p;
+                    spins = 0;
+                } else if (++spins > spin_limit) {
+                    atomicExch(&ctl->error, 1);
+                }
+                __nanosleep(256);
+            }
+            __syncthreads();
+            continue;
+        }
+        __threadfence();
+
+        const int g = s_g, rnd = s_rnd, v = s_v;
+        const GateDesc& d = gd[g];
+        GateOut* out = d.out;
+        const Tour tgr = tour_of<GB>(d);
+        const int m = tgr.m, n = tgr.n, nb = tgr.nb, P = tgr.P, R = tgr.R;
+        const int sweep = rnd / R, round = rnd - sweep * R;
+        float2* Wm = (float2*)d.W;
+        const double tol = tol_in > 0.0 ? tol_in : 2.0 * Eps<float>::v;
+        const float tol2 = (float)(tol * tol);
+        const float zthr = (float)(Eps<float>::v * Eps<float>::v * (double)max(m, n) * out->frob2);
+        const unsigned lim = d.wait_polls > 0 ? (unsigned)d.wait_polls : kGramSpin;
+
+        int I, J;
+        if (nb == 1) {
+            I = 0;
+            J = -1;
+        } else {
+            rr_pair(P, round, v, I, J);
+            if (I >= nb) { I = J; J = -1; }
+            else if (J >= nb) J = -1;
+            if (J >= 0 && J < I) { const int t = I; I = J; J = t; }
+        }
+        const bool intra = (round == 0);
+        if (J >= 0 || intra) {
+            const int colI = I * GB, nI = min(GB, n - colI);
+            const int colJ = J >= 0 ? J * GB : 0, nJ = J >= 0 ? min(GB, n - colJ) : 0;
+            // ---- 1. Gram matrix P = Y^T Y in TMEM columns [0, 64)
+            // rows 64..127 of the K-tile buffers stay zero (the 128-row MMA reads them)
+            for (int i = tid; i < 4 * 64 * 8; i += GT) {
+                const int t = i >> 9, r = 64 + ((i >> 3) & 63), c = i & 7;
+                *reinterpret_cast<float4*>(sm + OFF_A + t * TILE128 + r * 128 + c * 16) = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            const int nkt = (m + 31) / 32;
+            bool fail = false;
+            for (int kt = 0; kt < nkt && !fail; ++kt) {
+                const int b = kt & 1;
+                if (tid == 0) s_ok = wait_bar(b, lim);   // the MMAs of kt - 2 read this buffer
+                __syncthreads();
+                if (!s_ok) { fail = true; break; }
+                unsigned char* hi = sm + OFF_A + b * 2 * TILE128;
+                unsigned char* lo = hi + TILE128;
+                {
+                    const int c = tid >> 4, rr = (tid & 15) * 2, row = kt * 32 + rr;
+                    const int gc = vcol(c, colI, nI, colJ, nJ);
+                    float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (gc >= 0 && row < m) x = __ldcg(reinterpret_cast<const float4*>(Wm + (size_t)gc * m + row));
+                    st_split(hi, lo, sw128_off(c, rr), x.x);
+                    st_split(hi, lo, sw128_off(c, rr + 1), x.z);
+                    st_split(hi, lo, sw128_off(GC + c, rr), x.y);
+                    st_split(hi, lo, sw128_off(GC + c, rr + 1), x.w);
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncthreads();
+                if (tid == 0) {
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t ah = sbase + OFF_A + b * 2 * TILE128, al = ah + TILE128;
+                    mma_ktile(t_gram, ah, al, ah, al, idesc, kt == 0);
+                    mma_commit(b ? bar1 : bar0);
+                    pend[b] = true;
+                }
+            }
+            if (!fail) {
+                if (tid == 0) s_ok = wait_bar(0, lim) && wait_bar(1, lim);
+                __syncthreads();
+                fail = !s_ok;
+            }
+            if (fail) {
+                // drain what is still in flight, then leave with the gate unfinished
+                if (tid == 0) {
+                    wait_bar(0, kGramSpin);
+                    wait_bar(1, kGramSpin);
+                    out->status = 5;
+                    atomicExch(&ctl->error, 1);
+                    s_fail = 1;
+                }
+                __syncthreads();
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (warp < 2) {
+                const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+                float* prow = Ps + (warp * 32 + lane) * 65;
+#pragma unroll
+                for (int c0 = 0; c0 < 64; c0 += 16) {
+                    float vv[16];
+                    tmem_ld16(t_gram + lane_off + c0, vv);
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) prow[c0 + e] = vv[e];
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncthreads();
+            for (int e = tid; e < GC * GC; e += GT) {
+                const int i = e >> 5, j = e & 31;
+                const float gr = Ps[i * 65 + j] + Ps[(GC + i) * 65 + GC + j];
+                const float gi = Ps[i * 65 + GC + j] - Ps[(GC + i) * 65 + j];
+                Gb[i * GS + j] = make_float2(gr, gi);
+                Db[i * GS + j] = make_float2(0.f, 0.f);
+            }
+            __syncthreads();
+            // ---- 2. the visit's rotations on G, accumulated in D = V - I
+            int cur = 0, nstep = 0;
+            auto run_step = [&](int step, bool stin) {
+                const int sp = nstep++ & 1;
+                PairPrm* prm = s_prm[sp];
+                if (warp == 0) {
+                    const int p = lane, q = partner_of(p, step, stin);
+                    const bool vp = p < GB ? p < nI : p - GB < nJ, vq = q < GB ? q < nI : q - GB < nJ;
+                    const bool exam = p < q && vp && vq;
+                    int rot = 0;
+                    if (p < q) {
+                        PairPrm pr{0.f, 0.f, 0.f, 0.f, 0};
+                        if (exam) {
+                            const float2* G = Gb + cur * GC * GS;
+                            const float2 gq = G[p * GS + q];
+                            rot = rot_params_fast(G[p * GS + p].x, G[q * GS + q].x, gq.x, gq.y, tol2, zthr, pr.cm1,
+                                                  pr.sr, pr.si, pr.tg);
+                            pr.rot = rot;
+                        }
+                        prm[p] = pr;
+                    }
+                    const unsigned rb = __ballot_sync(0xffffffffu, rot), eb = __ballot_sync(0xffffffffu, exam);
+                    if (lane == 0) {
+                        s_any[sp] = rb != 0u;
+                        s_rot += __popc(rb);
+                        s_vis += __popc(eb);
+                    }
+                }
+                __syncthreads();
+                if (!s_any[sp]) return;   // G and D unchanged
+                const float2* G = Gb + cur * GC * GS;
+                const float2* D = Db + cur * GC * GS;
+                float2* Gn = Gb + (cur ^ 1) * GC * GS;
+                float2* Dn = Db + (cur ^ 1) * GC * GS;
+                for (int e = tid; e < GC * GC; e += GT) {
+                    const int p = e >> 5, q = e & 31;
+                    const Fac fp = fac_of(prm, p, step, stin), fq = fac_of(prm, q, step, stin);
+                    const int pp = fp.part, qq = fq.part;
+                    // G J: (G J)_{aq} = G_aq + H_aq, H_aq = cm1_q G_aq + G_aq' off_q
+                    const float2 g_pq = G[p * GS + q], g_pqq = G[p * GS + qq];
+                    const float2 g_ppq = G[pp * GS + q], g_ppqq = G[pp * GS + qq];
+                    const float2 h_p = cadd(make_float2(fq.cm1 * g_pq.x, fq.cm1 * g_pq.y), cmul(g_pqq, fq.off));
+                    const float2 h_pp = cadd(make_float2(fq.cm1 * g_ppq.x, fq.cm1 * g_ppq.y), cmul(g_ppqq, fq.off));
+                    // J^H (G J): G'_pq = G_pq + [H_pq + cm1_p (G_pq + H_pq) + conj(off_p) (G_p'q + H_p'q)]
+                    const float2 gj_p = cadd(g_pq, h_p), gj_pp = cadd(g_ppq, h_pp);
+                    const float2 corr = cadd(cadd(h_p, make_float2(fp.cm1 * gj_p.x, fp.cm1 * gj_p.y)), cmulc(fp.off, gj_pp));
+                    float2 ng = cadd(g_pq, corr);
+                    if (fp.rot && q == p) ng = make_float2(g_pq.x + (fp.first ? -fp.tg : fp.tg), 0.f);
+                    if (fp.rot && q == pp) ng = make_float2(0.f, 0.f);
+                    Gn[p * GS + q] = ng;
+                    // D J + (J - I): D'_pq = D_pq + [cm1_q D_pq + D_pq' off_q + (J - I)_pq]
+                    const float2 d_pq = D[p * GS + q], d_pqq = D[p * GS + qq];
+                    float2 dc = cadd(make_float2(fq.cm1 * d_pq.x, fq.cm1 * d_pq.y), cmul(d_pqq, fq.off));
+                    if (p == q) dc.x += fq.cm1;
+                    if (p == qq) dc = cadd(dc, fq.off);
+                    Dn[p * GS + q] = cadd(d_pq, dc);
+                }
+                __syncthreads();
+                cur ^= 1;
+            };
+            if (intra)
+                for (int t = 0; t < GB - 1; ++t) run_step(t, true);
+            if (J >= 0)
+                for (int sft = 0; sft < GB; ++sft) run_step(sft, false);
+            // ---- 3. X <- X + X D on the tensor cores (only if anything rotated)
+            if (s_rot > 0) {
+                const float2* D = Db + cur * GC * GS;
+                // B tiles: row n, K index k of R_D^T, R_D = [[Re D, Im D], [-Im D, Re D]] (K x N = 64 x 64)
+                for (int e = tid; e < 64 * 64; e += GT) {
+                    const int nn = e >> 6, k = e & 63;
+                    const float2 dv = D[(k & 31) * GS + (nn & 31)];
+                    const float val = k < GC ? (nn < GC ? dv.x : dv.y) : (nn < GC ? -dv.y : dv.x);
+                    unsigned char* bh = sm + OFF_B_AL + (k >> 5) * 2 * TILE64;
+                    st_split(bh, bh + TILE64, sw128_off(nn, k & 31), val);
+                }
+                const int nrc = (m + 127) / 128;
+                for (int rc = 0; rc < nrc && !fail; ++rc) {
+                    const int r0 = rc * 128;
+                    // A tiles: row (matrix row - r0), K index k: k < 32 Re X[., k], else Im X[., k - 32]
+                    {
+                        const int c = tid >> 4, rr = (tid & 15) * 8;
+                        const int gc = vcol(c, colI, nI, colJ, nJ);
+#pragma unroll
+                        for (int h = 0; h < 4; ++h) {
+                            const int rl = rr + 2 * h, row = r0 + rl;
+                            float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+                            if (gc >= 0 && row < m) x = __ldcg(reinterpret_cast<const float4*>(Wm + (size_t)gc * m + row));
+                            unsigned char* a0 = sm + OFF_A;               // K tile 0 (Re): hi, lo
+                            unsigned char* a1 = sm + OFF_A + 2 * TILE128; // K tile 1 (Im): hi, lo
+                            st_split(a0, a0 + TILE128, sw128_off(rl, c), x.x);
+                            st_split(a1, a1 + TILE128, sw128_off(rl, c), x.y);
+                            st_split(a0, a0 + TILE128, sw128_off(rl + 1, c), x.z);
+                            st_split(a1, a1 + TILE128, sw128_off(rl + 1, c), x.w);
+                        }
+                    }
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    __syncthreads();
+                    if (tid == 0) {
+                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+                        for (int kt = 0; kt < 2; ++kt) {
+                            const uint32_t ah = sbase + OFF_A + kt * 2 * TILE128, al = ah + TILE128;
+                            const uint32_t bh = sbase + OFF_B_AL + kt * 2 * TILE64, bl = bh + TILE64;
+                            mma_ktile(t_upd, ah, al, bh, bl, idesc, kt == 0);
+                        }
+                        mma_commit(bar0);
+                        pend[0] = true;
+                        s_ok = wait_bar(0, lim);
+                    }
+                    __syncthreads();
+                    if (!s_ok) {
+                        fail = true;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    if (warp < 4) {
+                        const int row = r0 + warp * 32 + lane;
+                        const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+                        float cr[32], ci[32];
+                        tmem_ld16(t_upd + lane_off + 0, *reinterpret_cast<float(*)[16]>(cr));
+                        tmem_ld16(t_upd + lane_off + 16, *reinterpret_cast<float(*)[16]>(cr + 16));
+                        tmem_ld16(t_upd + lane_off + 32, *reinterpret_cast<float(*)[16]>(ci));
+                        tmem_ld16(t_upd + lane_off + 48, *reinterpret_cast<float(*)[16]>(ci + 16));
+                        if (row < m) {
+#pragma unroll 4
+                            for (int c = 0; c < GC; ++c) {
+                                const int gc = vcol(c, colI, nI, colJ, nJ);
+                                if (gc < 0) continue;
+                                float2* w = Wm + (size_t)gc * m + row;
+                                const float2 x = __ldcg(w);
+                                __stcg(w, make_float2(x.x + cr[c], x.y + ci[c]));
+                            }
+                        }
+                    }
+                    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                    __syncthreads();
+                }
+                if (fail) {
+                    if (tid == 0) {
+                        wait_bar(0, kGramSpin);
+                        out->status = 5;
+                        atomicExch(&ctl->error, 1);
+                        s_fail = 1;
+                    }
+                    __syncthreads();
+                    break;
+                }
+            }
+        }
+        __threadfence();   // every thread's column stores before the report
+        __syncthreads();
+        if (tid == 0) {
+            if (s_rot) {
+                atomicAdd(&out->rot_sweep, s_rot);
+                atomicAdd(&out->rotations, (unsigned long long)s_rot);
+            }
+            if (s_vis) atomicAdd(&out->visits, (unsigned long long)s_vis);
+            __threadfence();
+            const int dn = atomicAdd(&out->done, 1) + 1;
+            if (dn == tgr.V) {
+                out->done = 0;
+                bool fin = false;
+                if (round == R - 1) {
+                    const int rs = atomicExch(&out->rot_sweep, 0);
+                    if (rs == 0 || sweep + 1 >= max_sweeps) {
+                        fin = true;
+                        out->sweeps = sweep + 1;
+                        if (rs != 0 && out->status < 4) out->status = 4;
+                    }
+                }
+                __threadfence();
+                if (fin) {
+                    atomicExch(&out->finished, 1);
+                    atomicAdd(&ctl->n_finished, 1);
+                } else {
+                    atomicExch(&out->claim, (unsigned long long)(rnd + 1) << 32);
+                }
+                atomicAdd(&ctl->progress, 1u);
+            }
+        }
+        __syncthreads();
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(s_tmem), "r"(128));
+}
+
+// Launch: one CTA of 512 threads per SM (about 197 KB of shared memory), no more CTAs
+// than visits of a round can use.
+cudaError_t launch_jacobi_tc(const GateDesc* d, int n_gates, int n_lead, int n_max, double tol, int max_sweeps,
+                             JacobiCtl* ctl, cudaStream_t s, unsigned spin_limit) {
+    if (n_gates <= 0) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_jacobi_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi_tc, GT, SMEM_BYTES)) != cudaSuccess)
+        return e;
+    if (per_sm < 1) return cudaErrorLaunchOutOfResources;
+    const int nb = (n_max + GB - 1) / GB;
+    const long long visits = (long long)n_gates * ((nb == 1) ? 1 : (nb + (nb & 1)) / 2);
+    long long grid = (long long)sms;   // one CTA per SM: each holds 128 TMEM columns and most of the shared memory
+    if (grid > visits) grid = visits;
+    if (grid < 1) grid = 1;
+    const int lead = (n_lead < 1 || n_lead > n_gates) ? n_gates : n_lead;
+    k_jacobi_tc<<<(unsigned)grid, GT, SMEM_BYTES, s>>>(d, n_gates, lead, tol, max_sweeps < 1 ? 1 : max_sweeps, ctl,
+                                                       spin_limit ? spin_limit : kSpinLimit);
+    return cudaGetLastError();
+}
+
+}  // namespace tnsim

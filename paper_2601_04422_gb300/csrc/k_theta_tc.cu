@@ -29,6 +29,7 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include "tc_common.cuh"
 #include "tnsim_internal.h"
 
 namespace tnsim {
@@ -39,17 +40,7 @@ constexpr int TC_N = 2 * TC_RH;    // output tile columns
 constexpr int TC_THREADS = 128;
 constexpr unsigned kTcSpin = 1u << 26;     // default polls of a bounded mbarrier wait (about a second)
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
 // ---------------------------------------------------------------- split pass
-
-__device__ __forceinline__ float tf32_round(float v) {
-    uint32_t b = __float_as_uint(v);
-    b = (b + 0x0FFFu + ((b >> 13) & 1u)) & 0xFFFFE000u;   // round to nearest even, 10-bit mantissa
-    return __uint_as_float(b);
-}
 
 template <int MODE>  // 0: TF32 (planes of fp32 words), 1: BF16
 struct PlaneT;
@@ -127,27 +118,6 @@ __global__ void __launch_bounds__(256) k_split(const GateDesc* __restrict__ gd) 
 
 // ---------------------------------------------------------------- tcgen05 GEMM
 
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-// One poll is one non-blocking test of the phase (mbarrier.test_wait), so a limit
-// counts checks, not an implementation-defined suspend time.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase, unsigned limit) {
-    for (unsigned i = 0; i < limit; ++i) {
-        uint32_t done;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-            " selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done)
-            : "r"(bar), "r"(phase)
-            : "memory");
-        if (done) return true;
-    }
-    return false;
-}
 __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y, int z,
                                             uint32_t bar) {
     asm volatile(
@@ -157,22 +127,8 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map
         : "memory");
 }
 
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((addr >> 4) & 0x3FFFu);
-    d |= (uint64_t)1 << 16;                       // leading byte offset (unused for this layout)
-    d |= (uint64_t)((1024u >> 4) & 0x3FFFu) << 32;  // stride byte offset: 8 rows x 128 B
-    d |= (uint64_t)1 << 46;                       // descriptor version for tcgen05
-    d |= (uint64_t)2 << 61;                       // 128-byte swizzle
-    return d;
-}
-
-// Instruction descriptor: FP32 accumulator, A and B of format fmt, both K-major.
-__device__ __forceinline__ uint32_t inst_desc(uint32_t fmt, uint32_t negA) {
-    return (1u << 4) | (fmt << 7) | (fmt << 10) | (negA << 13) | ((uint32_t)(TC_N >> 3) << 17) |
-           ((uint32_t)(TC_M >> 4) << 24);
-}
+// Instruction descriptor of this kernel's 128 x 128 tiles.
+__device__ __forceinline__ uint32_t inst_desc(uint32_t fmt, uint32_t negA) { return idesc_mn(fmt, negA, TC_M, TC_N); }
 
 template <int MODE>
 __device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
@@ -187,19 +143,6 @@ __device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uin
             " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
             "l"(a), "l"(b), "r"(idesc), "r"(acc));
     }
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
-        "%13, %14, %15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 template <int MODE>

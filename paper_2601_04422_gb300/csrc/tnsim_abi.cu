@@ -1485,6 +1485,13 @@ tnsim_status tnsim_autotune(tnsim_mps* m, int32_t n2, const int32_t* q, const do
     int best = 0;
     cudaError_t e = cudaSuccess;
     for (int c = 0; c < kJacobiConfigs && e == cudaSuccess; ++c) {
+        // configurations that launch the same kernels as an earlier one are not re-timed:
+        // bit 0 with the tensor-core visits, and bit 2 for complex128 (no such path)
+        const int same = (c & 4) ? (m->dt == TNSIM_C128 ? (c & 3) : ((c & 1) ? c - 1 : -1)) : -1;
+        if (same >= 0) {
+            if (ms_out) ms_out[c] = ms_out ? ms_out[same] : 0.0;
+            continue;
+        }
         double cmin = 0.0;
         for (int r = 0; r < reps && e == cudaSuccess; ++r) {
             for (int i = 0; i < n2 && e == cudaSuccess; ++i)

@@ -131,10 +131,11 @@ struct Site1Desc {
 template <typename T>
 cudaError_t launch_theta(const GateDesc* d, int n_gates, int chiL_max, int chiR_max,
                          cudaStream_t s);
-// cfg selects the block width / CTAs per SM (0: wide blocks, 1 CTA per SM; 1: half-width
-// blocks, 2 CTAs per SM).  The configurations a state can select add QR preconditioning
-// (bit 1 of the state's configuration, GateDesc::qr): kJacobiConfigs of them.
-constexpr int kJacobiConfigs = 4;
+// cfg bit 0 selects the block width / CTAs per SM (0: wide blocks, 1 CTA per SM; 1:
+// half-width blocks, 2 CTAs per SM); bit 2 (complex64 only) the Gram-matrix visits with
+// tensor-core block products (k_jacobi_tc.cu; bit 0 then has no effect).  Bit 1 of a
+// state's configuration adds QR preconditioning (GateDesc::qr): kJacobiConfigs of them.
+constexpr int kJacobiConfigs = 8;
 // n_lead: how many leading descriptors (sorted by decreasing size) share the first one's
 // size; the persistent CTAs start spread over them (0: over all gates).
 // spin_limit: idle polls without progress before an idle CTA gives up (0 = default).
@@ -142,6 +143,9 @@ template <typename T>
 cudaError_t launch_jacobi(const GateDesc* d, int n_gates, int m_max, int n_max, double tol,
                           int max_sweeps, JacobiCtl* ctl, cudaStream_t s, int cfg = 0, int n_lead = 0,
                           unsigned spin_limit = 0);
+// the tensor-core Jacobi launch (complex64), called by launch_jacobi<float> for cfg bit 2
+cudaError_t launch_jacobi_tc(const GateDesc* d, int n_gates, int n_lead, int n_max, double tol, int max_sweeps,
+                             JacobiCtl* ctl, cudaStream_t s, unsigned spin_limit);
 // n_max: the largest 2 chi_R of the batch (grid of the column-norm pass)
 template <typename T>
 cudaError_t launch_truncate(const GateDesc* d, int n_gates, int n_max, cudaStream_t s);

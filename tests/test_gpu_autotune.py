@@ -27,7 +27,7 @@ def _all_bits(n):
     return np.array([[(x >> (n - 1 - i)) & 1 for i in range(n)] for x in range(2 ** n)], dtype=np.uint8)
 
 
-@pytest.mark.parametrize("cfg", [0, 1, 2, 3])
+@pytest.mark.parametrize("cfg", range(8))
 def test_every_configuration_exact_complex128(T, cfg):
     circ, p = W.config_c1(2)
     m = T.MPS(10, dtype=T.TNSIM_C128, chi_max=p["chi_max"])
@@ -39,7 +39,7 @@ def test_every_configuration_exact_complex128(T, cfg):
     m.close()
 
 
-@pytest.mark.parametrize("cfg", [0, 1, 2, 3])
+@pytest.mark.parametrize("cfg", range(8))
 def test_every_configuration_exact_complex128_wide_blocks(T, cfg):
     """14 qubits without truncation (bonds up to 128, gated blocks up to 256 rows,
     several column blocks per gate in every configuration): the dense state vector
@@ -56,7 +56,7 @@ def test_every_configuration_exact_complex128_wide_blocks(T, cfg):
     m.close()
 
 
-@pytest.mark.parametrize("cfg", [0, 1, 2, 3])
+@pytest.mark.parametrize("cfg", range(8))
 def test_every_configuration_complex64_per_layer(T, cfg):
     """24 qubits, chi 64 (m up to 128): every layer against the oracle on the same input."""
     circ = W.brickwork_u2_su4(24, 9, seed=6)

@@ -53,14 +53,16 @@ def test_qr_layers_complex128(T, cfg):
     m.close()
 
 
-def test_qr_saturated_layers_complex64(T):
+@pytest.mark.parametrize("cfg", [2, 6])
+def test_qr_saturated_layers_complex64(T, cfg):
     """40 qubits at chi 128 (square 256 x 256 gated blocks in the bulk), complex64,
-    tensor-core contraction: the layers after the bond dimension saturates."""
+    tensor-core contraction: the layers after the bond dimension saturates (with the
+    column rotations, and with the Gram-matrix visits on the tensor cores)."""
     n = 40
     circ = W.brickwork_su4(n, 11, seed=5)
     m = T.MPS(n, dtype=T.TNSIM_C64, chi_max=128, gemm=T.TNSIM_GEMM_TF32X3)
     m.run(W.Circuit(n, circ.layers[:8]))
-    T.tnsim_set_jacobi_config(m.h, 2)
+    T.tnsim_set_jacobi_config(m.h, cfg)
     for lay in circ.layers[8:]:
         _check_layer(m, lay, 128, 1e-5, 1e-6, 1e-4)
     m.close()
