@@ -697,7 +697,11 @@ def run_ours(args, world, rank, local):
         cfg["jacobi_config"] = {"chosen": int(tune_choice), "autotune_ms": [float(x) for x in tune_ms],
                                 "configs": ["16-column blocks, 1 CTA/SM", "8-column blocks, 2 CTAs/SM",
                                             "16-column blocks, 1 CTA/SM, QR-preconditioned",
-                                            "8-column blocks, 2 CTAs/SM, QR-preconditioned"]}
+                                            "8-column blocks, 2 CTAs/SM, QR-preconditioned",
+                                            "Gram-matrix visits, tcgen05 block products",
+                                            "same as 4 (bit 0 has no effect)",
+                                            "Gram-matrix visits, tcgen05 block products, QR-preconditioned",
+                                            "same as 6 (bit 0 has no effect)"]}
         cfg["interior_chi"] = int(np.max(dims))
         cfg["discarded_weight_per_gate"] = disc_mean
         cfg["contraction"] = {"fp32": "FP32 FMA (4M)", "fp32_3m": "FP32 FMA (3M)",

@@ -524,7 +524,8 @@ cudaError_t launch_jacobi(const GateDesc* d, int n_gates, int m_max, int n_max, 
                           unsigned spin_limit) {
     if (n_gates <= 0) return cudaSuccess;
     if constexpr (sizeof(T) == 4) {
-        if (cfg & 4) return launch_jacobi_tc(d, n_gates, n_lead, n_max, tol, max_sweeps, ctl, s, spin_limit);
+        if ((cfg & 4) && m_max <= jacobi_tc_max_rows())
+            return launch_jacobi_tc(d, n_gates, n_lead, n_max, tol, max_sweeps, ctl, s, spin_limit);
     }
     const bool narrow = (cfg & 1) != 0;
 #define TNSIM_JAC(BC, RPL, MINB) launch_bc<T, BC, RPL, MINB>(d, n_gates, n_lead, m_max, n_max, tol, max_sweeps, ctl, s, spin_limit)

@@ -21,8 +21,8 @@
 //      in 3xTF32, chunks of 128 rows, the correction added to X in the epilogue (so a
 //      column that barely moves keeps its bits).  A visit that rotates nothing writes
 //      nothing back.
-// Each visit reads its columns twice (once for G, once for the update) and writes them
-// once; the rotation steps touch only the 32 x 32 matrices in shared memory.
+// Both blocks are staged in shared memory once per visit (asynchronous 16-byte copies),
+// so m <= 512; the rotation steps touch only the 32 x 32 matrices.
 //
 // Operand tiles are written by the threads into 128-byte-swizzled K-major layout (the
 // layout a SWIZZLE_128B TMA copy produces), made visible to the tensor cores with a
@@ -45,37 +45,46 @@ constexpr int GB = 16;                 // columns per block
 constexpr int GC = 2 * GB;             // complex columns of a visit
 constexpr int GT = 512;                // threads of a CTA
 constexpr int GS = GC + 1;             // row stride of the 32 x 32 matrices in shared memory
+constexpr int GM = 512;                // largest m (rows) the staged blocks hold
 constexpr unsigned kGramSpin = 1u << 26;
 
 // dynamic shared memory (1024-byte aligned base)
 constexpr uint32_t TILE128 = 128 * 128;                 // 128 rows x 128 bytes
 constexpr uint32_t TILE64 = 64 * 128;                   // 64 rows x 128 bytes
-constexpr uint32_t OFF_A = 0;                           // 4 x TILE128: Gram K-tiles / update A tiles
-constexpr uint32_t OFF_P = 4 * TILE128;                 // 64 x 65 floats: Y^T Y read back from TMEM
-constexpr uint32_t OFF_B = OFF_P + 64 * 65 * 4 + 256;   // 4 x TILE64: update B tiles (1024-aligned below)
-constexpr uint32_t OFF_B_AL = (OFF_B + 1023) / 1024 * 1024;
-constexpr uint32_t OFF_G = OFF_B_AL + 4 * TILE64;       // 2 x 32 x 33 float2
-constexpr uint32_t OFF_D = OFF_G + 2 * GC * GS * 8;     // 2 x 32 x 33 float2
-constexpr uint32_t SMEM_USED = OFF_D + 2 * GC * GS * 8;
+constexpr uint32_t OFF_X = 0;                           // staged blocks: 32 columns x m complex
+constexpr uint32_t OFF_T = GC * GM * 8;                 // 64 KB of tiles, 1024-aligned
+// Gram phase: K-tile buffer b (hi, lo) at OFF_T + b * 2 TILE128; after it, P = Y^T Y
+// (64 x 65 floats) at OFF_T.  Update phase: A tiles (hi, lo) of one K tile at OFF_T, the
+// B tiles (K tile kt, hi / lo) at OFF_B + (2 kt + hl) TILE64.
+constexpr uint32_t OFF_B = OFF_T + 2 * TILE128;
+constexpr uint32_t OFF_G = OFF_T + 4 * TILE128;         // G: two buffers of 32 x 33 float2
+constexpr uint32_t OFF_D = OFF_G + 2 * GC * GS * 8;     // D: 32 x 33 float2 (updated in place)
+constexpr uint32_t SMEM_USED = OFF_D + GC * GS * 8;
 constexpr uint32_t SMEM_BYTES = SMEM_USED + 1024;       // slack for aligning the base
 
 struct PairPrm {
     float cm1, sr, si, tg;
-    int rot;
+    int q1, q2, rot;
 };
 
-// Partner of index p (0..31) in a step.  Cross step sft: column w of block I meets
-// column (w + sft) mod 16 of block J.  Intra step t: the circle-method pair of round t
-// among the 16 columns of each block (rr_pair(16, t, .)); its inverse: 15 <-> t, and
-// x <-> (2t - x) mod 15 otherwise.
-__device__ __forceinline__ int partner_of(int p, int step, bool intra) {
-    if (!intra) return p < GB ? GB + (p + step) % GB : (p - GB - step + 2 * GB) % GB;
-    const int base = p < GB ? 0 : GB, x = p - base;
-    const int y = x == GB - 1 ? step : (x == step ? GB - 1 : (2 * step - x + 2 * (GB - 1)) % (GB - 1));
-    return base + y;
+// Pair w (0..15) of a step, q1 < q2.  Cross step sft: column w of block I and column
+// (w + sft) mod 16 of block J.  Intra step t: the circle-method pairs of round t among
+// the 16 columns of each block (rr_pair(16, t, .)), w < 8 in block I, w >= 8 in block J.
+__device__ __forceinline__ void pair_of(int w, int step, bool intra, int& q1, int& q2) {
+    if (!intra) {
+        q1 = w;
+        q2 = GB + (w + step) % GB;
+        return;
+    }
+    const int base = w < GB / 2 ? 0 : GB;
+    int a, b;
+    rr_pair(GB, step, w & (GB / 2 - 1), a, b);
+    q1 = base + min(a, b);
+    q2 = base + max(a, b);
 }
 
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 cscale(float s, float2 a) { return make_float2(s * a.x, s * a.y); }
 // a * b
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
@@ -85,36 +94,10 @@ __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
     return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.x, b.y, -a.y * b.x));
 }
 
-// The rotation factors of index x in the current step: J_xx = 1 + cm1 and the
-// off-diagonal entry J_{x' x} of its column (x' its partner): -conj(s e) if x is the
-// pair's first index, s e if it is the second.  Zero when the pair does not rotate.
-struct Fac {
-    float cm1;
-    float2 off;
-    int rot, first, part;
-    float tg;
-};
-__device__ __forceinline__ Fac fac_of(const PairPrm* prm, int x, int step, bool intra) {
-    Fac f;
-    f.part = partner_of(x, step, intra);
-    f.first = x < f.part;
-    const PairPrm& q = prm[f.first ? x : f.part];
-    f.rot = q.rot;
-    f.cm1 = q.rot ? q.cm1 : 0.f;
-    f.tg = q.tg;
-    f.off = q.rot ? (f.first ? make_float2(-q.sr, q.si) : make_float2(q.sr, q.si)) : make_float2(0.f, 0.f);
-    return f;
-}
-
 __device__ __forceinline__ void st_split(unsigned char* hi_tile, unsigned char* lo_tile, uint32_t off, float v) {
     const float h = tf32_round(v);
     *reinterpret_cast<float*>(hi_tile + off) = h;
     *reinterpret_cast<float*>(lo_tile + off) = tf32_round(v - h);
-}
-
-// local column c (0..31) of a visit -> column of W, or -1 past the end of a block
-__device__ __forceinline__ int vcol(int c, int colI, int nI, int colJ, int nJ) {
-    return c < GB ? (c < nI ? colI + c : -1) : (c - GB < nJ ? colJ + c - GB : -1);
 }
 
 // issue (one thread) the 3xTF32 products of one 32-wide K tile: D += Ahi Bhi + Ahi Blo + Alo Bhi
@@ -143,15 +126,17 @@ k_jacobi_tc(const GateDesc* __restrict__ gd, int n_gates, int n_lead, double tol
             JacobiCtl* __restrict__ ctl, unsigned spin_limit) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* sm = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    float* Ps = reinterpret_cast<float*>(sm + OFF_P);
-    float2* Gb = reinterpret_cast<float2*>(sm + OFF_G);   // two buffers of GC x GS
-    float2* Db = reinterpret_cast<float2*>(sm + OFF_D);
+    float2* Xs = reinterpret_cast<float2*>(sm + OFF_X);    // column c of the visit at Xs + c m
+    float* Ps = reinterpret_cast<float*>(sm + OFF_T);
+    float2* Gb = reinterpret_cast<float2*>(sm + OFF_G);
+    float2* Ds = reinterpret_cast<float2*>(sm + OFF_D);
     const uint32_t sbase = smem_u32(sm);
     __shared__ int s_g, s_rnd, s_v, s_exit, s_rot, s_vis, s_fail, s_ok;
-    // per step (double-buffered by the step's parity: warp 0 may write a step's entries
-    // while slower warps still read the previous step's, never two steps ahead)
+    // per step, double-buffered by the step's parity: warp 0 may write a step's entries
+    // while slower warps still read the previous step's, never two steps ahead
     __shared__ int s_any[2];
-    __shared__ PairPrm s_prm[2][GC];
+    __shared__ PairPrm s_prm[2][GB];
+    __shared__ int s_ix[2][GC];        // index -> 2 * (its pair) + (second of the pair)
     __shared__ short s_V[kScanTable];
     __shared__ __align__(8) uint64_t s_bar[2];
     __shared__ uint32_t s_tmem;
@@ -176,8 +161,8 @@ k_jacobi_tc(const GateDesc* __restrict__ gd, int n_gates, int n_lead, double tol
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t t_gram = s_tmem, t_upd = s_tmem + 64;
     const uint32_t idesc = idesc_mn(2u, 0u, 128, 64);
-    uint32_t ph[2] = {0u, 0u};         // parity of the next completion of each barrier
-    bool pend[2] = {false, false};     // a commit on the barrier not yet waited for
+    uint32_t ph[2] = {0u, 0u};         // (thread 0) parity of the next completion of each barrier
+    bool pend[2] = {false, false};     // (thread 0) a commit on the barrier not yet waited for
     const uint32_t bar0 = smem_u32(&s_bar[0]), bar1 = smem_u32(&s_bar[1]);
 
     // (thread 0) bounded wait for the outstanding commit on barrier b; false on timeout
@@ -251,29 +236,35 @@ k_jacobi_tc(const GateDesc* __restrict__ gd, int n_gates, int n_lead, double tol
             if (J >= 0 && J < I) { const int t = I; I = J; J = t; }
         }
         const bool intra = (round == 0);
+        bool fail = false;
         if (J >= 0 || intra) {
             const int colI = I * GB, nI = min(GB, n - colI);
             const int colJ = J >= 0 ? J * GB : 0, nJ = J >= 0 ? min(GB, n - colJ) : 0;
-            // ---- 1. Gram matrix P = Y^T Y in TMEM columns [0, 64)
-            // rows 64..127 of the K-tile buffers stay zero (the 128-row MMA reads them)
+            auto valid = [&](int c) { return c < GB ? c < nI : c - GB < nJ; };
+            copy_blocks_in(Xs, Wm + (size_t)colI * m, nI * m, Xs + (size_t)GB * m, Wm + (size_t)colJ * m,
+                           J >= 0 ? nJ * m : 0);
+            // rows 64..127 of the four 128-row tiles are zero for the Gram products
             for (int i = tid; i < 4 * 64 * 8; i += GT) {
                 const int t = i >> 9, r = 64 + ((i >> 3) & 63), c = i & 7;
-                *reinterpret_cast<float4*>(sm + OFF_A + t * TILE128 + r * 128 + c * 16) = make_float4(0.f, 0.f, 0.f, 0.f);
+                *reinterpret_cast<float4*>(sm + OFF_T + t * TILE128 + r * 128 + c * 16) = make_float4(0.f, 0.f, 0.f, 0.f);
             }
+            __syncthreads();
+            // ---- 1. P = Y^T Y in TMEM columns [0, 64), K tiles of 32 rows, two tile buffers
             const int nkt = (m + 31) / 32;
-            bool fail = false;
-            for (int kt = 0; kt < nkt && !fail; ++kt) {
+            for (int kt = 0; kt < nkt; ++kt) {
                 const int b = kt & 1;
-                if (tid == 0) s_ok = wait_bar(b, lim);   // the MMAs of kt - 2 read this buffer
+                if (tid == 0) s_ok = wait_bar(b, lim);   // the products of tile kt - 2 read this buffer
                 __syncthreads();
-                if (!s_ok) { fail = true; break; }
-                unsigned char* hi = sm + OFF_A + b * 2 * TILE128;
+                if (!s_ok) {
+                    fail = true;
+                    break;
+                }
+                unsigned char* hi = sm + OFF_T + b * 2 * TILE128;
                 unsigned char* lo = hi + TILE128;
                 {
                     const int c = tid >> 4, rr = (tid & 15) * 2, row = kt * 32 + rr;
-                    const int gc = vcol(c, colI, nI, colJ, nJ);
                     float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (gc >= 0 && row < m) x = __ldcg(reinterpret_cast<const float4*>(Wm + (size_t)gc * m + row));
+                    if (valid(c) && row < m) x = *reinterpret_cast<const float4*>(Xs + (size_t)c * m + row);
                     st_split(hi, lo, sw128_off(c, rr), x.x);
                     st_split(hi, lo, sw128_off(c, rr + 1), x.z);
                     st_split(hi, lo, sw128_off(GC + c, rr), x.y);
@@ -283,7 +274,7 @@ k_jacobi_tc(const GateDesc* __restrict__ gd, int n_gates, int n_lead, double tol
                 __syncthreads();
                 if (tid == 0) {
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint32_t ah = sbase + OFF_A + b * 2 * TILE128, al = ah + TILE128;
+                    const uint32_t ah = sbase + OFF_T + b * 2 * TILE128, al = ah + TILE128;
                     mma_ktile(t_gram, ah, al, ah, al, idesc, kt == 0);
                     mma_commit(b ? bar1 : bar0);
                     pend[b] = true;
@@ -294,60 +285,53 @@ k_jacobi_tc(const GateDesc* __restrict__ gd, int n_gates, int n_lead, double tol
                 __syncthreads();
                 fail = !s_ok;
             }
-            if (fail) {
-                // drain what is still in flight, then leave with the gate unfinished
-                if (tid == 0) {
-                    wait_bar(0, kGramSpin);
-                    wait_bar(1, kGramSpin);
-                    out->status = 5;
-                    atomicExch(&ctl->error, 1);
-                    s_fail = 1;
+            if (!fail) {
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                if (warp < 2) {
+                    const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+                    float* prow = Ps + (warp * 32 + lane) * 65;
+#pragma unroll
+                    for (int c0 = 0; c0 < 64; c0 += 16) {
+                        float vv[16];
+                        tmem_ld16(t_gram + lane_off + c0, vv);
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) prow[c0 + e] = vv[e];
+                    }
+                }
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncthreads();
+                for (int e = tid; e < GC * GC; e += GT) {
+                    const int i = e >> 5, j = e & 31;
+                    const float gr = Ps[i * 65 + j] + Ps[(GC + i) * 65 + GC + j];
+                    const float gi = Ps[i * 65 + GC + j] - Ps[(GC + i) * 65 + j];
+                    Gb[i * GS + j] = make_float2(gr, gi);
+                    Ds[i * GS + j] = make_float2(0.f, 0.f);
                 }
                 __syncthreads();
-                break;
             }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            if (warp < 2) {
-                const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
-                float* prow = Ps + (warp * 32 + lane) * 65;
-#pragma unroll
-                for (int c0 = 0; c0 < 64; c0 += 16) {
-                    float vv[16];
-                    tmem_ld16(t_gram + lane_off + c0, vv);
-#pragma unroll
-                    for (int e = 0; e < 16; ++e) prow[c0 + e] = vv[e];
-                }
-            }
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            __syncthreads();
-            for (int e = tid; e < GC * GC; e += GT) {
-                const int i = e >> 5, j = e & 31;
-                const float gr = Ps[i * 65 + j] + Ps[(GC + i) * 65 + GC + j];
-                const float gi = Ps[i * 65 + GC + j] - Ps[(GC + i) * 65 + j];
-                Gb[i * GS + j] = make_float2(gr, gi);
-                Db[i * GS + j] = make_float2(0.f, 0.f);
-            }
-            __syncthreads();
             // ---- 2. the visit's rotations on G, accumulated in D = V - I
             int cur = 0, nstep = 0;
             auto run_step = [&](int step, bool stin) {
                 const int sp = nstep++ & 1;
                 PairPrm* prm = s_prm[sp];
+                int* ix = s_ix[sp];
                 if (warp == 0) {
-                    const int p = lane, q = partner_of(p, step, stin);
-                    const bool vp = p < GB ? p < nI : p - GB < nJ, vq = q < GB ? q < nI : q - GB < nJ;
-                    const bool exam = p < q && vp && vq;
-                    int rot = 0;
-                    if (p < q) {
-                        PairPrm pr{0.f, 0.f, 0.f, 0.f, 0};
-                        if (exam) {
+                    int rot = 0, exam = 0;
+                    if (lane < GB) {
+                        int q1, q2;
+                        pair_of(lane, step, stin, q1, q2);
+                        PairPrm pr{0.f, 0.f, 0.f, 0.f, q1, q2, 0};
+                        if (valid(q1) && valid(q2)) {
+                            exam = 1;
                             const float2* G = Gb + cur * GC * GS;
-                            const float2 gq = G[p * GS + q];
-                            rot = rot_params_fast(G[p * GS + p].x, G[q * GS + q].x, gq.x, gq.y, tol2, zthr, pr.cm1,
+                            const float2 gq = G[q1 * GS + q2];
+                            rot = rot_params_fast(G[q1 * GS + q1].x, G[q2 * GS + q2].x, gq.x, gq.y, tol2, zthr, pr.cm1,
                                                   pr.sr, pr.si, pr.tg);
                             pr.rot = rot;
                         }
-                        prm[p] = pr;
+                        prm[lane] = pr;
+                        ix[q1] = 2 * lane;
+                        ix[q2] = 2 * lane + 1;
                     }
                     const unsigned rb = __ballot_sync(0xffffffffu, rot), eb = __ballot_sync(0xffffffffu, exam);
                     if (lane == 0) {
@@ -358,124 +342,147 @@ k_jacobi_tc(const GateDesc* __restrict__ gd, int n_gates, int n_lead, double tol
                 }
                 __syncthreads();
                 if (!s_any[sp]) return;   // G and D unchanged
+                // thread: row p of G and D, the two columns q1 < q2 of pair w
+                const int p = tid >> 4, w = tid & 15;
+                const PairPrm qw = prm[w];
+                const int pix = ix[p];
+                const PairPrm pw = prm[pix >> 1];
+                const bool psec = pix & 1;
+                const int pp = psec ? pw.q1 : pw.q2;
+                // J_{q2 q1} = -conj(s e), J_{q1 q2} = s e, J_qq = 1 + cm1 (zero factors if not rotated)
+                const float cq = qw.rot ? qw.cm1 : 0.f;
+                const float2 off1 = qw.rot ? make_float2(-qw.sr, qw.si) : make_float2(0.f, 0.f);
+                const float2 off2 = qw.rot ? make_float2(qw.sr, qw.si) : make_float2(0.f, 0.f);
+                const float cp = pw.rot ? pw.cm1 : 0.f;
+                const float2 offp = pw.rot ? (psec ? make_float2(pw.sr, pw.si) : make_float2(-pw.sr, pw.si))
+                                           : make_float2(0.f, 0.f);   // J_{p' p}
+                const int q1 = qw.q1, q2 = qw.q2;
                 const float2* G = Gb + cur * GC * GS;
-                const float2* D = Db + cur * GC * GS;
                 float2* Gn = Gb + (cur ^ 1) * GC * GS;
-                float2* Dn = Db + (cur ^ 1) * GC * GS;
-                for (int e = tid; e < GC * GC; e += GT) {
-                    const int p = e >> 5, q = e & 31;
-                    const Fac fp = fac_of(prm, p, step, stin), fq = fac_of(prm, q, step, stin);
-                    const int pp = fp.part, qq = fq.part;
-                    // G J: (G J)_{aq} = G_aq + H_aq, H_aq = cm1_q G_aq + G_aq' off_q
-                    const float2 g_pq = G[p * GS + q], g_pqq = G[p * GS + qq];
-                    const float2 g_ppq = G[pp * GS + q], g_ppqq = G[pp * GS + qq];
-                    const float2 h_p = cadd(make_float2(fq.cm1 * g_pq.x, fq.cm1 * g_pq.y), cmul(g_pqq, fq.off));
-                    const float2 h_pp = cadd(make_float2(fq.cm1 * g_ppq.x, fq.cm1 * g_ppq.y), cmul(g_ppqq, fq.off));
-                    // J^H (G J): G'_pq = G_pq + [H_pq + cm1_p (G_pq + H_pq) + conj(off_p) (G_p'q + H_p'q)]
-                    const float2 gj_p = cadd(g_pq, h_p), gj_pp = cadd(g_ppq, h_pp);
-                    const float2 corr = cadd(cadd(h_p, make_float2(fp.cm1 * gj_p.x, fp.cm1 * gj_p.y)), cmulc(fp.off, gj_pp));
-                    float2 ng = cadd(g_pq, corr);
-                    if (fp.rot && q == p) ng = make_float2(g_pq.x + (fp.first ? -fp.tg : fp.tg), 0.f);
-                    if (fp.rot && q == pp) ng = make_float2(0.f, 0.f);
-                    Gn[p * GS + q] = ng;
-                    // D J + (J - I): D'_pq = D_pq + [cm1_q D_pq + D_pq' off_q + (J - I)_pq]
-                    const float2 d_pq = D[p * GS + q], d_pqq = D[p * GS + qq];
-                    float2 dc = cadd(make_float2(fq.cm1 * d_pq.x, fq.cm1 * d_pq.y), cmul(d_pqq, fq.off));
-                    if (p == q) dc.x += fq.cm1;
-                    if (p == qq) dc = cadd(dc, fq.off);
-                    Dn[p * GS + q] = cadd(d_pq, dc);
+                const float2 a1 = G[p * GS + q1], a2 = G[p * GS + q2];
+                const float2 b1 = G[pp * GS + q1], b2 = G[pp * GS + q2];
+                // (G J)_{x q} = G_xq + H_xq
+                const float2 ha1 = cadd(cscale(cq, a1), cmul(a2, off1)), ha2 = cadd(cscale(cq, a2), cmul(a1, off2));
+                const float2 hb1 = cadd(cscale(cq, b1), cmul(b2, off1)), hb2 = cadd(cscale(cq, b2), cmul(b1, off2));
+                // (J^H G J)_{pq} = G_pq + [H_pq + cm1_p (G J)_pq + conj(J_{p'p}) (G J)_{p'q}]
+                float2 n1 = cadd(a1, cadd(cadd(ha1, cscale(cp, cadd(a1, ha1))), cmulc(offp, cadd(b1, hb1))));
+                float2 n2 = cadd(a2, cadd(cadd(ha2, cscale(cp, cadd(a2, ha2))), cmulc(offp, cadd(b2, hb2))));
+                if (qw.rot && p == q1) {
+                    n1 = make_float2(a1.x - qw.tg, 0.f);
+                    n2 = make_float2(0.f, 0.f);
+                } else if (qw.rot && p == q2) {
+                    n1 = make_float2(0.f, 0.f);
+                    n2 = make_float2(a2.x + qw.tg, 0.f);
+                }
+                Gn[p * GS + q1] = n1;
+                Gn[p * GS + q2] = n2;
+                if (qw.rot) {
+                    // D <- D J + (J - I), in place (this thread alone owns D[p][q1], D[p][q2])
+                    const float2 d1 = Ds[p * GS + q1], d2 = Ds[p * GS + q2];
+                    float2 c1 = cadd(cscale(cq, d1), cmul(d2, off1));
+                    float2 c2 = cadd(cscale(cq, d2), cmul(d1, off2));
+                    if (p == q1) {
+                        c1.x += cq;
+                        c2 = cadd(c2, off2);
+                    } else if (p == q2) {
+                        c1 = cadd(c1, off1);
+                        c2.x += cq;
+                    }
+                    Ds[p * GS + q1] = cadd(d1, c1);
+                    Ds[p * GS + q2] = cadd(d2, c2);
                 }
                 __syncthreads();
                 cur ^= 1;
             };
-            if (intra)
-                for (int t = 0; t < GB - 1; ++t) run_step(t, true);
-            if (J >= 0)
-                for (int sft = 0; sft < GB; ++sft) run_step(sft, false);
+            if (!fail) {
+                if (intra)
+                    for (int t = 0; t < GB - 1; ++t) run_step(t, true);
+                if (J >= 0)
+                    for (int sft = 0; sft < GB; ++sft) run_step(sft, false);
+            }
             // ---- 3. X <- X + X D on the tensor cores (only if anything rotated)
-            if (s_rot > 0) {
-                const float2* D = Db + cur * GC * GS;
+            if (!fail && s_rot > 0) {
                 // B tiles: row n, K index k of R_D^T, R_D = [[Re D, Im D], [-Im D, Re D]] (K x N = 64 x 64)
                 for (int e = tid; e < 64 * 64; e += GT) {
                     const int nn = e >> 6, k = e & 63;
-                    const float2 dv = D[(k & 31) * GS + (nn & 31)];
+                    const float2 dv = Ds[(k & 31) * GS + (nn & 31)];
                     const float val = k < GC ? (nn < GC ? dv.x : dv.y) : (nn < GC ? -dv.y : dv.x);
-                    unsigned char* bh = sm + OFF_B_AL + (k >> 5) * 2 * TILE64;
+                    unsigned char* bh = sm + OFF_B + (k >> 5) * 2 * TILE64;
                     st_split(bh, bh + TILE64, sw128_off(nn, k & 31), val);
                 }
                 const int nrc = (m + 127) / 128;
                 for (int rc = 0; rc < nrc && !fail; ++rc) {
                     const int r0 = rc * 128;
-                    // A tiles: row (matrix row - r0), K index k: k < 32 Re X[., k], else Im X[., k - 32]
-                    {
-                        const int c = tid >> 4, rr = (tid & 15) * 8;
-                        const int gc = vcol(c, colI, nI, colJ, nJ);
+                    for (int kt = 0; kt < 2; ++kt) {
+                        // A tile of K tile kt: row (matrix row - r0), K index c: Re X (kt 0) / Im X (kt 1)
+                        {
+                            unsigned char* ah = sm + OFF_T;
+                            unsigned char* al = ah + TILE128;
+                            const int c = tid >> 4, rr = (tid & 15) * 8;
+                            const bool vc = valid(c);
 #pragma unroll
-                        for (int h = 0; h < 4; ++h) {
-                            const int rl = rr + 2 * h, row = r0 + rl;
-                            float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
-                            if (gc >= 0 && row < m) x = __ldcg(reinterpret_cast<const float4*>(Wm + (size_t)gc * m + row));
-                            unsigned char* a0 = sm + OFF_A;               // K tile 0 (Re): hi, lo
-                            unsigned char* a1 = sm + OFF_A + 2 * TILE128; // K tile 1 (Im): hi, lo
-                            st_split(a0, a0 + TILE128, sw128_off(rl, c), x.x);
-                            st_split(a1, a1 + TILE128, sw128_off(rl, c), x.y);
-                            st_split(a0, a0 + TILE128, sw128_off(rl + 1, c), x.z);
-                            st_split(a1, a1 + TILE128, sw128_off(rl + 1, c), x.w);
+                            for (int h = 0; h < 4; ++h) {
+                                const int rl = rr + 2 * h, row = r0 + rl;
+                                float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+                                if (vc && row < m) x = *reinterpret_cast<const float4*>(Xs + (size_t)c * m + row);
+                                st_split(ah, al, sw128_off(rl, c), kt ? x.y : x.x);
+                                st_split(ah, al, sw128_off(rl + 1, c), kt ? x.w : x.z);
+                            }
                         }
-                    }
-                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    __syncthreads();
-                    if (tid == 0) {
-                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-#pragma unroll
-                        for (int kt = 0; kt < 2; ++kt) {
-                            const uint32_t ah = sbase + OFF_A + kt * 2 * TILE128, al = ah + TILE128;
-                            const uint32_t bh = sbase + OFF_B_AL + kt * 2 * TILE64, bl = bh + TILE64;
+                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                        __syncthreads();
+                        if (tid == 0) {
+                            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                            const uint32_t ah = sbase + OFF_T, al = ah + TILE128;
+                            const uint32_t bh = sbase + OFF_B + kt * 2 * TILE64, bl = bh + TILE64;
                             mma_ktile(t_upd, ah, al, bh, bl, idesc, kt == 0);
+                            mma_commit(bar0);
+                            pend[0] = true;
+                            s_ok = wait_bar(0, lim);   // the next A tile reuses the buffer
                         }
-                        mma_commit(bar0);
-                        pend[0] = true;
-                        s_ok = wait_bar(0, lim);
+                        __syncthreads();
+                        if (!s_ok) {
+                            fail = true;
+                            break;
+                        }
                     }
-                    __syncthreads();
-                    if (!s_ok) {
-                        fail = true;
-                        break;
-                    }
+                    if (fail) break;
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    if (warp < 4) {
-                        const int row = r0 + warp * 32 + lane;
-                        const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
-                        float cr[32], ci[32];
-                        tmem_ld16(t_upd + lane_off + 0, *reinterpret_cast<float(*)[16]>(cr));
-                        tmem_ld16(t_upd + lane_off + 16, *reinterpret_cast<float(*)[16]>(cr + 16));
-                        tmem_ld16(t_upd + lane_off + 32, *reinterpret_cast<float(*)[16]>(ci));
-                        tmem_ld16(t_upd + lane_off + 48, *reinterpret_cast<float(*)[16]>(ci + 16));
+                    {
+                        // every warp: lanes of its TMEM quarter (rows), 8 of the 32 columns
+                        const int qtr = warp & 3, cg = warp >> 2;
+                        const int row = r0 + qtr * 32 + lane;
+                        const uint32_t lane_off = (uint32_t)(qtr * 32) << 16;
+                        float cr[8], ci[8];
+                        tmem_ld8(t_upd + lane_off + 8 * cg, cr);
+                        tmem_ld8(t_upd + lane_off + GC + 8 * cg, ci);
                         if (row < m) {
-#pragma unroll 4
-                            for (int c = 0; c < GC; ++c) {
-                                const int gc = vcol(c, colI, nI, colJ, nJ);
-                                if (gc < 0) continue;
-                                float2* w = Wm + (size_t)gc * m + row;
-                                const float2 x = __ldcg(w);
-                                __stcg(w, make_float2(x.x + cr[c], x.y + ci[c]));
+#pragma unroll
+                            for (int e = 0; e < 8; ++e) {
+                                const int c = 8 * cg + e;
+                                if (!valid(c)) continue;
+                                const int gc = c < GB ? colI + c : colJ + c - GB;
+                                const float2 x = Xs[(size_t)c * m + row];
+                                __stcg(Wm + (size_t)gc * m + row, make_float2(x.x + cr[e], x.y + ci[e]));
                             }
                         }
                     }
                     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                     __syncthreads();
                 }
-                if (fail) {
-                    if (tid == 0) {
-                        wait_bar(0, kGramSpin);
-                        out->status = 5;
-                        atomicExch(&ctl->error, 1);
-                        s_fail = 1;
-                    }
-                    __syncthreads();
-                    break;
-                }
             }
+        }
+        if (fail) {
+            // drain what is still in flight, then leave with the gate unfinished
+            if (tid == 0) {
+                wait_bar(0, kGramSpin);
+                wait_bar(1, kGramSpin);
+                out->status = 5;
+                atomicExch(&ctl->error, 1);
+                s_fail = 1;
+            }
+            __syncthreads();
+            break;
         }
         __threadfence();   // every thread's column stores before the report
         __syncthreads();
@@ -515,8 +522,8 @@ k_jacobi_tc(const GateDesc* __restrict__ gd, int n_gates, int n_lead, double tol
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(s_tmem), "r"(128));
 }
 
-// Launch: one CTA of 512 threads per SM (about 197 KB of shared memory), no more CTAs
-// than visits of a round can use.
+// Launch: one CTA of 512 threads per SM (about 222 KB of shared memory); no more CTAs
+// than visits of a round can use.  Gates of more than 512 rows take the column kernel.
 cudaError_t launch_jacobi_tc(const GateDesc* d, int n_gates, int n_lead, int n_max, double tol, int max_sweeps,
                              JacobiCtl* ctl, cudaStream_t s, unsigned spin_limit) {
     if (n_gates <= 0) return cudaSuccess;
@@ -538,5 +545,7 @@ cudaError_t launch_jacobi_tc(const GateDesc* d, int n_gates, int n_lead, int n_m
                                                        spin_limit ? spin_limit : kSpinLimit);
     return cudaGetLastError();
 }
+
+int jacobi_tc_max_rows() { return GM; }
 
 }  // namespace tnsim

@@ -146,6 +146,8 @@ cudaError_t launch_jacobi(const GateDesc* d, int n_gates, int m_max, int n_max, 
 // the tensor-core Jacobi launch (complex64), called by launch_jacobi<float> for cfg bit 2
 cudaError_t launch_jacobi_tc(const GateDesc* d, int n_gates, int n_lead, int n_max, double tol, int max_sweeps,
                              JacobiCtl* ctl, cudaStream_t s, unsigned spin_limit);
+// the largest m (= 2 chi_L) the tensor-core Jacobi launch takes; larger gates run k_jacobi
+int jacobi_tc_max_rows();
 // n_max: the largest 2 chi_R of the batch (grid of the column-norm pass)
 template <typename T>
 cudaError_t launch_truncate(const GateDesc* d, int n_gates, int n_max, cudaStream_t s);
