@@ -48,7 +48,8 @@ METRIC = "2-qubit gates/s at χ=256 (contract+SVD+truncate), % roofline, vs plai
 UNIT = "2q gates/s"
 N_QUBITS, CHI, PRESAT = 100, 256, 10
 HEA_CUTOFF = 1e-10          # discarded-weight cutoff of the gradient workload
-JACOBI_SRC = os.path.join(ROOT, "paper_2601_04422_gb300", "csrc", "k_jacobi.cu")
+# the column kernel and the scheduling header it includes (hashed together)
+JACOBI_SRC = [os.path.join(ROOT, "paper_2601_04422_gb300", "csrc", f) for f in ("k_jacobi.cu", "jacobi_sched.cuh")]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_jacobi_chi256.md")
 
 
@@ -129,7 +130,7 @@ def jacobi_traffic():
     m2 = re.search(r"source_sha256:\s*([0-9a-f]{64})", txt)
     if not (m1 and m2):
         return None
-    sha = hashlib.sha256(open(JACOBI_SRC, "rb").read()).hexdigest()
+    sha = hashlib.sha256(b"".join(open(f, "rb").read() for f in JACOBI_SRC)).hexdigest()
     return float(m1.group(1)) if sha == m2.group(1) else None
 
 
