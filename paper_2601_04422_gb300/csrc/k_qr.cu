@@ -229,19 +229,27 @@ __global__ void __launch_bounds__(QT, 1) k_qr(const GateDesc* __restrict__ gd) {
         }
         __syncthreads();
         if (warp == 0 && lane < NB) {
+            // lane i builds row i of T; the row stays in registers (fully unrolled loops),
+            // so the recurrence's only shared-memory reads are the independent Zm entries
             const int i = lane;
+            C trow[NB];
+#pragma unroll
             for (int j = 0; j < NB; ++j) {
                 C t = cz<C>();
                 if (i < j) {
                     C acc = cz<C>();
-                    for (int l = i; l < j; ++l) cmac(acc, Tm[i][l], Zm[l][j]);
+#pragma unroll
+                    for (int l = 0; l < j; ++l)
+                        if (l >= i) cmac(acc, trow[l], Zm[l][j]);
                     t.x = -s_tau[j] * acc.x;
                     t.y = -s_tau[j] * acc.y;
                 } else if (i == j) {
                     t.x = s_tau[j];
                 }
-                Tm[i][j] = t;
+                trow[j] = t;
             }
+#pragma unroll
+            for (int j = 0; j < NB; ++j) Tm[i][j] = trow[j];
         }
         __syncthreads();
         // ---- trailing update A <- (I - V T^H V^H) A, WC columns per warp task, the tasks
