@@ -418,15 +418,16 @@ k_jacobi_tc(const GateDesc* __restrict__ gd, int n_gates, int n_lead, double tol
                         {
                             unsigned char* ah = sm + OFF_T;
                             unsigned char* al = ah + TILE128;
-                            const int c = tid >> 4, rr = (tid & 15) * 8;
+                            // rows 16 h + (tid & 15): the 16 threads of a column store into
+                            // rows of eight different swizzle phases (no 16-way bank conflict)
+                            const int c = tid >> 4, rb = tid & 15;
                             const bool vc = valid(c);
 #pragma unroll
-                            for (int h = 0; h < 4; ++h) {
-                                const int rl = rr + 2 * h, row = r0 + rl;
-                                float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
-                                if (vc && row < m) x = *reinterpret_cast<const float4*>(Xs + (size_t)c * m + row);
+                            for (int h = 0; h < 8; ++h) {
+                                const int rl = rb + 16 * h, row = r0 + rl;
+                                float2 x = make_float2(0.f, 0.f);
+                                if (vc && row < m) x = Xs[(size_t)c * m + row];
                                 st_split(ah, al, sw128_off(rl, c), kt ? x.y : x.x);
-                                st_split(ah, al, sw128_off(rl + 1, c), kt ? x.w : x.z);
                             }
                         }
                         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");

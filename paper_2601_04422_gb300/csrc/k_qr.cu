@@ -465,11 +465,17 @@ cudaError_t launch_qr(const GateDesc* d, int n_gates, int m_max, cudaStream_t s)
 }
 
 template <typename T>
-cudaError_t launch_sites_pre(const GateDesc* d, int n_gates, int m_max, int k_max, int n_max, cudaStream_t s) {
+cudaError_t launch_sites_pre(const GateDesc* d, int n_gates, int m_max, int k_max, int n_max, cudaStream_t s,
+                             int tc) {
     if (n_gates <= 0) return cudaSuccess;
-    dim3 g1((m_max + 63) / 64, (k_max + 63) / 64, n_gates);
-    k_left_pre<T><<<g1, 256, 0, s>>>(d);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e;
+    if (sizeof(T) == 4 && tc) {
+        e = launch_left_pre_tc(d, n_gates, m_max, k_max, s);   // tensor cores (k_sites_tc.cu)
+    } else {
+        dim3 g1((m_max + 63) / 64, (k_max + 63) / 64, n_gates);
+        k_left_pre<T><<<g1, 256, 0, s>>>(d);
+        e = cudaGetLastError();
+    }
     if (e != cudaSuccess) return e;
     dim3 g2((unsigned)std::max(1, std::min(64, (k_max * n_max + 255) / 256)), n_gates);
     k_right_pre<T><<<g2, 256, 0, s>>>(d);
@@ -478,7 +484,7 @@ cudaError_t launch_sites_pre(const GateDesc* d, int n_gates, int m_max, int k_ma
 
 template cudaError_t launch_qr<float>(const GateDesc*, int, int, cudaStream_t);
 template cudaError_t launch_qr<double>(const GateDesc*, int, int, cudaStream_t);
-template cudaError_t launch_sites_pre<float>(const GateDesc*, int, int, int, int, cudaStream_t);
-template cudaError_t launch_sites_pre<double>(const GateDesc*, int, int, int, int, cudaStream_t);
+template cudaError_t launch_sites_pre<float>(const GateDesc*, int, int, int, int, cudaStream_t, int);
+template cudaError_t launch_sites_pre<double>(const GateDesc*, int, int, int, int, cudaStream_t, int);
 
 }  // namespace tnsim

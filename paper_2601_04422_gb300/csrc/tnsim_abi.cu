@@ -364,7 +364,9 @@ tnsim_status launch_gates(cudaStream_t st, const std::vector<GateJob>& jobs, con
     ev = prof_begin(pm, st);
     CUDA_TRY(launch_right<T>(d_desc, ng, k_max, n_max, st));
     if (canon) CUDA_TRY(launch_left_canon<T>(d_desc, ng, m_max, k_max, st));
-    if (qr) CUDA_TRY(launch_sites_pre<T>(d_desc, ng, m_max, k_max, n_max, st));
+    if (qr)
+        CUDA_TRY(launch_sites_pre<T>(d_desc, ng, m_max, k_max, n_max, st,
+                                     pm->p.gemm == TNSIM_GEMM_TF32X3 || pm->p.gemm == TNSIM_GEMM_BF16X3));
     prof_end(pm, st, TNSIM_K_RIGHT, ev);
     // bounds for the next layer
     for (const GateJob& j : jobs) {
@@ -1057,7 +1059,9 @@ tnsim_status tnsim_plan_launch(tnsim_plan* p) {
         CUDA_TRY(launch_left<float>(p->d_desc, ng, m_max, p->k_max, st));
         CUDA_TRY(launch_right<float>(p->d_desc, ng, p->k_max, n_max, st));
         if (p->canon) CUDA_TRY(launch_left_canon<float>(p->d_desc, ng, m_max, p->k_max, st));
-        if (p->qr) CUDA_TRY(launch_sites_pre<float>(p->d_desc, ng, m_max, p->k_max, n_max, st));
+        if (p->qr)
+            CUDA_TRY(launch_sites_pre<float>(p->d_desc, ng, m_max, p->k_max, n_max, st,
+                                             p->gemm == TNSIM_GEMM_TF32X3 || p->gemm == TNSIM_GEMM_BF16X3));
     }
     // the bond upper bounds the host keeps become the capacities
     for (tnsim_mps* m : p->states)

@@ -166,7 +166,10 @@ cudaError_t launch_left_canon(const GateDesc* d, int n_gates, int m_max, int k_m
 template <typename T>
 cudaError_t launch_qr(const GateDesc* d, int n_gates, int m_max, cudaStream_t s);
 template <typename T>
-cudaError_t launch_sites_pre(const GateDesc* d, int n_gates, int m_max, int k_max, int n_max, cudaStream_t s);
+cudaError_t launch_sites_pre(const GateDesc* d, int n_gates, int m_max, int k_max, int n_max, cudaStream_t s,
+                             int tc = 0);
+// the left site of the QR-preconditioned complex64 gates on the tensor cores (3xTF32)
+cudaError_t launch_left_pre_tc(const GateDesc* d, int n_gates, int m_max, int k_max, cudaStream_t s);
 template <typename T>
 cudaError_t launch_site1q(const Site1Desc* d, int n_sites, int cap_lr, cudaStream_t s);
 
