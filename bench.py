@@ -495,13 +495,15 @@ def run_ours(args, world, rank, local):
                 "avg_launch_ms": jac_ms / max(jac_n, 1),
                 "profiled_layers": n_prof}
     # ---- whole-gate roofline time T* (contraction on the tensor pipe at the TF32 rate;
-    # QR preconditioning, Jacobi and site product on the FP32 ALUs; site reads and writes
-    # at HBM rate)
+    # QR preconditioning and Jacobi on the FP32 ALUs; the site product on the tensor pipe
+    # when the QR configurations run it there (tensor-core contraction modes), else on the
+    # FP32 ALUs; site reads and writes at HBM rate)
     ng = max(stats["gates"], 1)
     tf32_peak = pk["bf16_tflops_sustained"] * (1.1 / 2.25)          # nominal TF32 : BF16 dense ratio
+    site_tc = bool(int(tune_choice) & 2) and args.gemm in ("tf32x3", "bf16x3")
     t_contract = 8.0 * stats["theta_cmacs"] / ng / (tf32_peak * 1e12)
     t_svd = flops / ng / (peak * 1e12)
-    t_right = 8.0 * stats["right_cmacs"] / ng / (peak * 1e12)
+    t_right = 8.0 * stats["right_cmacs"] / ng / ((tf32_peak if site_tc else peak) * 1e12)
     t_qr = 8.0 * stats["qr_cmacs"] / ng / (peak * 1e12)
     site_bytes = 4.0 * 2 * CHI * CHI * 8                             # read A, B; write A', B' (complex64)
     t_mem = site_bytes / (pk["hbm_gbs"] * 1e9)
@@ -509,7 +511,8 @@ def run_ours(args, world, rank, local):
     path_roofline = {"t_star_us_per_gate": t_star * 1e6, "gates_per_s_at_roofline": 1.0 / t_star,
                      "frac": value / (1.0 / t_star),
                      "parts_us": {"contraction_tf32": t_contract * 1e6, "qr_fp32": t_qr * 1e6,
-                                  "jacobi_fp32": t_svd * 1e6, "site_product_fp32": t_right * 1e6,
+                                  "jacobi_fp32": t_svd * 1e6,
+                                  ("site_product_tf32" if site_tc else "site_product_fp32"): t_right * 1e6,
                                   "site_bytes_hbm": t_mem * 1e6},
                      "peaks": f"TF32 {tf32_peak:.0f} TFLOP/s (measured sustained BF16 x 1.1/2.25), FP32 ALU "
                               f"{peak:.1f} TFLOP/s, HBM {pk['hbm_gbs']:.0f} GB/s"}
