@@ -288,9 +288,11 @@ tnsim_status tnsim_set_jacobi_config(tnsim_mps* m, int32_t cfg);
  *                       complete before it sets the launch's error flag; every CTA then
  *                       leaves, the unfinished gates report status 5;
  *   mbarrier_polls    : polls of one mbarrier wait (TMA copies landed, MMAs done) in the
- *                       tensor-core contraction; on timeout the CTA waits (with the default
- *                       limit) for the copies or MMAs it already issued, then leaves and
- *                       reports status 5 for its gate.
+ *                       tensor-core kernels (the contraction, the Gram-matrix Jacobi visits
+ *                       of configurations 4-7, the left site of the QR configurations); on
+ *                       timeout the CTA waits (with the default limit) for the copies or
+ *                       MMAs it already issued, then leaves and reports status 5 for its
+ *                       gate.
  * 0 restores a default (2^22 and 2^26 polls: about a second or more, far beyond any
  * legitimate wait).
  * Calls after a timeout return ETIMEOUT; the state is undefined but the handle and

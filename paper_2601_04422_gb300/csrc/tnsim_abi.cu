@@ -701,7 +701,7 @@ tnsim_status tnsim_apply_layer(tnsim_mps* m, int32_t n2, const int32_t* q, const
         worst = std::max(worst, m->h_out[i].status);
     }
     if (worst) CUDA_TRY(cudaMemset(m->d_sticky, 0, sizeof(int)));
-    if (worst == 5) return fail(TNSIM_ETIMEOUT, "the Jacobi kernel's idle CTAs saw no progress (layer incomplete)");
+    if (worst == 5) return fail(TNSIM_ETIMEOUT, "a bounded device wait ran out: an idle Jacobi CTA saw no progress or a tensor-core wait expired (layer incomplete)");
     if (worst == 4) return fail(TNSIM_ENOCONV, "a Jacobi SVD reached max_sweeps (layer applied)");
     return TNSIM_OK;
 }
@@ -764,7 +764,7 @@ tnsim_status tnsim_apply_circuit(tnsim_mps* m, int32_t n_ops, const int32_t* qa,
     for (double e : eps) tot += e;
     if (eps_sum_out) *eps_sum_out = tot;
     if (sticky) CUDA_TRY(cudaMemset(m->d_sticky, 0, sizeof(int)));
-    if (sticky == 5) return fail(TNSIM_ETIMEOUT, "the Jacobi kernel's idle CTAs saw no progress (circuit incomplete)");
+    if (sticky == 5) return fail(TNSIM_ETIMEOUT, "a bounded device wait ran out: an idle Jacobi CTA saw no progress or a tensor-core wait expired (circuit incomplete)");
     if (sticky == 4) return fail(TNSIM_ENOCONV, "a Jacobi SVD reached max_sweeps (circuit applied)");
     return TNSIM_OK;
 }
@@ -919,7 +919,7 @@ tnsim_status tnsim_apply_layers_batched(tnsim_mps* const* ms, int32_t n_circ, in
         if (s != TNSIM_OK) return s;
         CUDA_TRY(cudaMemsetAsync(ms[i]->d_sticky, 0, sizeof(int), ms[i]->stream));
     }
-    if (worst == 5) return fail(TNSIM_ETIMEOUT, "the Jacobi kernel's idle CTAs saw no progress (step incomplete)");
+    if (worst == 5) return fail(TNSIM_ETIMEOUT, "a bounded device wait ran out: an idle Jacobi CTA saw no progress or a tensor-core wait expired (step incomplete)");
     if (worst == 4) return fail(TNSIM_ENOCONV, "a Jacobi SVD reached max_sweeps (steps applied)");
     return TNSIM_OK;
 }
@@ -1137,7 +1137,7 @@ tnsim_status tnsim_sync(tnsim_mps* m) {
     int sticky = 0;
     CUDA_TRY(cudaMemcpy(&sticky, m->d_sticky, sizeof(int), cudaMemcpyDeviceToHost));
     CUDA_TRY(cudaMemset(m->d_sticky, 0, sizeof(int)));
-    if (sticky == 5) return fail(TNSIM_ETIMEOUT, "the Jacobi kernel's idle CTAs saw no progress (layer incomplete)");
+    if (sticky == 5) return fail(TNSIM_ETIMEOUT, "a bounded device wait ran out: an idle Jacobi CTA saw no progress or a tensor-core wait expired (layer incomplete)");
     if (sticky) return fail(TNSIM_ENOCONV, "a Jacobi SVD reached max_sweeps (layer applied)");
     return TNSIM_OK;
 }
@@ -1675,7 +1675,7 @@ tnsim_status tnsim_grad(const tnsim_circuit* c, const double* theta, const tnsim
     int sticky = 0;
     CUDA_TRY(cudaMemcpyAsync(&sticky, m->d_sticky, sizeof(int), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
-    if (sticky == 5) return fail(TNSIM_ETIMEOUT, "the Jacobi kernel saw no progress (forward incomplete)");
+    if (sticky == 5) return fail(TNSIM_ETIMEOUT, "a bounded device wait ran out: an idle Jacobi CTA saw no progress or a tensor-core wait expired (forward incomplete)");
     auto chi_at = [&](int L, int b) { return chi_h[(size_t)L * (n + 1) + b]; };
     // ---- energy and the adjoint of the final state (environments of the final state)
     const int* dchi = m->d_chi;   // the final bond dimensions
