@@ -95,75 +95,9 @@ __device__ __forceinline__ int rotate_pair(C* __restrict__ xi, C* __restrict__ x
 __device__ __forceinline__ int reg_row(int lane, int k) { return 64 * (k >> 1) + 2 * lane + (k & 1); }
 
 // Rotation of a column pair whose first column lives in registers (layout above) and
-// whose second column lives in shared memory.  The second column is read once, kept
-// in registers for the update and written back once.  FULL: m == 32 * RPL, so no row
-// needs a bounds test.
-template <typename T, typename C, int RPL, bool FULL>
-__device__ __forceinline__ int rotate_reg(C (&xi)[RPL], C* __restrict__ xjs, int m, int lane,
-                                          T tol2, T zthr) {
-    C xj[RPL];
-    T a = 0, b = 0, gr = 0, gi = 0;
-#pragma unroll
-    for (int k = 0; k < RPL; k += 2) {
-        const int r = reg_row(lane, k);
-        if (FULL || r < m) {
-            // r and m are even: rows r and r + 1 are both present
-            if constexpr (sizeof(C) == 8) {
-                const float4 v = *reinterpret_cast<const float4*>(xjs + r);
-                xj[k].x = v.x; xj[k].y = v.y; xj[k + 1].x = v.z; xj[k + 1].y = v.w;
-            } else {
-                xj[k] = xjs[r];
-                xj[k + 1] = xjs[r + 1];
-            }
-        } else {
-            xj[k].x = 0; xj[k].y = 0; xj[k + 1].x = 0; xj[k + 1].y = 0;
-        }
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-            const C u = xi[k + e], v = xj[k + e];
-            a = fma(u.x, u.x, fma(u.y, u.y, a));
-            b = fma(v.x, v.x, fma(v.y, v.y, b));
-            gr = fma(u.x, v.x, fma(u.y, v.y, gr));
-            gi = fma(u.x, v.y, fma(-u.y, v.x, gi));
-        }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        a += __shfl_xor_sync(0xffffffffu, a, o);
-        b += __shfl_xor_sync(0xffffffffu, b, o);
-        gr += __shfl_xor_sync(0xffffffffu, gr, o);
-        gi += __shfl_xor_sync(0xffffffffu, gi, o);
-    }
-    T cm1, sr, si, tg;
-    if (!rot_params_fast(a, b, gr, gi, tol2, zthr, cm1, sr, si, tg)) return 0;
-    // same single-rounding update as rotate_pair
-#pragma unroll
-    for (int k = 0; k < RPL; k += 2) {
-        const int r = reg_row(lane, k);
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-            const C u = xi[k + e], v = xj[k + e];
-            C nu, nv;
-            nu.x = u.x + fma(-si, v.y, fma(-sr, v.x, cm1 * u.x));
-            nu.y = u.y + fma(si, v.x, fma(-sr, v.y, cm1 * u.y));
-            nv.x = v.x + fma(-si, u.y, fma(sr, u.x, cm1 * v.x));
-            nv.y = v.y + fma(si, u.x, fma(sr, u.y, cm1 * v.y));
-            xi[k + e] = nu;
-            xj[k + e] = nv;
-        }
-        if (FULL || r < m) {
-            if constexpr (sizeof(C) == 8) {
-                *reinterpret_cast<float4*>(xjs + r) = make_float4(xj[k].x, xj[k].y, xj[k + 1].x, xj[k + 1].y);
-            } else {
-                xjs[r] = xj[k];
-                xjs[r + 1] = xj[k + 1];
-            }
-        }
-    }
-    return 1;
-}
-
-// As rotate_reg, with the two column norms tracked instead of recomputed: a (the
+// whose second column lives in shared memory: the second column is read once, kept in
+// registers for the update and written back once (FULL: m == 32 * RPL, so no row needs
+// a bounds test).  The two column norms are tracked instead of recomputed: a (the
 // register column's, in a register) and *bj (the shared column's, in shared memory).
 // Only g = x_i^H x_j is formed; after a rotation the norms are a - t|g| and b + t|g|
 // (the eigenvalues of the pair's 2 x 2 Gram matrix).  The caller recomputes both
