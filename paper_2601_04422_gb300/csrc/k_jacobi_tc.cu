@@ -9,10 +9,12 @@
 // Jacobi rotations (Sec. IV.A; Hestenes), with the inner products taken from the Gram
 // matrix instead of the columns:
 //   1. G = X^H X on the tensor cores: with Y = [Re X | Im X] (m x 64 real), the product
-//      Y^T Y in 3xTF32 (hi.hi + hi.lo + lo.hi, FP32 accumulation in TMEM) over K tiles of
-//      32 rows; Re G = P11 + P22, Im G = P12 - P21.
+//      Y^T Y in 3xTF32 (hi.hi + hi.lo + lo.hi, FP32 accumulation in TMEM), each 128-row
+//      operand tile holding 32 rows of each half of Y (the diagonal blocks of its
+//      product are the two halves' contributions); Re G = P11 + P22, Im G = P12 - P21.
 //   2. The visit's rotations on G: a pair (i, j) takes a = G_ii, b = G_jj, g = G_ij and
-//      the rotation parameters of k_jacobi; a step's rotations J (16 disjoint pairs) give
+//      the rotation parameters of k_jacobi (every warp computes all 16 of a step and
+//      shares them by shuffles); a step's rotations J (16 disjoint pairs) give
 //      G <- J^H G J and D <- D J + (J - I), D = V - I the accumulated rotation minus the
 //      identity.  Every new entry is its old value plus a correction summed first (the
 //      single-rounding update of k_jacobi); the rotated pair's norms become a - t|g| and
@@ -62,11 +64,6 @@ constexpr uint32_t OFF_D = OFF_G + 2 * GC * GS * 8;     // D: 32 x 33 float2 (up
 constexpr uint32_t SMEM_USED = OFF_D + GC * GS * 8;
 constexpr uint32_t SMEM_BYTES = SMEM_USED + 1024;       // slack for aligning the base
 
-struct PairPrm {
-    float cm1, sr, si, tg;
-    int q1, q2, rot;
-};
-
 // Pair w (0..15) of a step, q1 < q2.  Cross step sft: column w of block I and column
 // (w + sft) mod 16 of block J.  Intra step t: the circle-method pairs of round t among
 // the 16 columns of each block (rr_pair(16, t, .)), w < 8 in block I, w >= 8 in block J.
@@ -81,6 +78,33 @@ __device__ __forceinline__ void pair_of(int w, int step, bool intra, int& q1, in
     rr_pair(GB, step, w & (GB / 2 - 1), a, b);
     q1 = base + min(a, b);
     q2 = base + max(a, b);
+}
+
+// Inverse of pair_of: the pair w of index x (0..31) in a step, and whether x is the
+// pair's second (larger) index.
+__device__ __forceinline__ void pair_index(int x, int step, bool intra, int& w, int& second) {
+    if (!intra) {
+        if (x < GB) {
+            w = x;
+            second = 0;
+        } else {
+            w = (x - GB - step + 2 * GB) % GB;
+            second = 1;
+        }
+        return;
+    }
+    const int base = x < GB ? 0 : GB, y = x - base;
+    int v, partner;
+    if (y == GB - 1 || y == step) {
+        v = 0;
+        partner = y == step ? GB - 1 : step;
+    } else {
+        const int v1 = (y - step + (GB - 1)) % (GB - 1);
+        v = v1 <= GB / 2 - 1 ? v1 : (step - y + (GB - 1)) % (GB - 1);
+        partner = (2 * step - y + 2 * (GB - 1)) % (GB - 1);
+    }
+    w = (base ? GB / 2 : 0) + v;
+    second = y > partner;
 }
 
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
@@ -132,11 +156,6 @@ k_jacobi_tc(const GateDesc* __restrict__ gd, int n_gates, int n_lead, double tol
     float2* Ds = reinterpret_cast<float2*>(sm + OFF_D);
     const uint32_t sbase = smem_u32(sm);
     __shared__ int s_g, s_rnd, s_v, s_exit, s_rot, s_vis, s_fail, s_ok;
-    // per step, double-buffered by the step's parity: warp 0 may write a step's entries
-    // while slower warps still read the previous step's, never two steps ahead
-    __shared__ int s_any[2];
-    __shared__ PairPrm s_prm[2][GB];
-    __shared__ int s_ix[2][GC];        // index -> 2 * (its pair) + (second of the pair)
     __shared__ short s_V[kScanTable];
     __shared__ __align__(8) uint64_t s_bar[2];
     __shared__ uint32_t s_tmem;
@@ -153,14 +172,14 @@ k_jacobi_tc(const GateDesc* __restrict__ gd, int n_gates, int n_lead, double tol
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
-                     "r"(128));
+                     "r"(256));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t t_gram = s_tmem, t_upd = s_tmem + 64;
-    const uint32_t idesc = idesc_mn(2u, 0u, 128, 64);
+    const uint32_t t_gram = s_tmem, t_upd = s_tmem + 128;   // 128 + 64 of the 256 columns held
+    const uint32_t idesc = idesc_mn(2u, 0u, 128, 64), idesc_g = idesc_mn(2u, 0u, 128, 128);
     uint32_t ph[2] = {0u, 0u};         // (thread 0) parity of the next completion of each barrier
     bool pend[2] = {false, false};     // (thread 0) a commit on the barrier not yet waited for
     const uint32_t bar0 = smem_u32(&s_bar[0]), bar1 = smem_u32(&s_bar[1]);
@@ -243,14 +262,14 @@ k_jacobi_tc(const GateDesc* __restrict__ gd, int n_gates, int n_lead, double tol
             auto valid = [&](int c) { return c < GB ? c < nI : c - GB < nJ; };
             copy_blocks_in(Xs, Wm + (size_t)colI * m, nI * m, Xs + (size_t)GB * m, Wm + (size_t)colJ * m,
                            J >= 0 ? nJ * m : 0);
-            // rows 64..127 of the four 128-row tiles are zero for the Gram products
-            for (int i = tid; i < 4 * 64 * 8; i += GT) {
-                const int t = i >> 9, r = 64 + ((i >> 3) & 63), c = i & 7;
-                *reinterpret_cast<float4*>(sm + OFF_T + t * TILE128 + r * 128 + c * 16) = make_float4(0.f, 0.f, 0.f, 0.f);
-            }
             __syncthreads();
-            // ---- 1. P = Y^T Y in TMEM columns [0, 64), K tiles of 32 rows, two tile buffers
-            const int nkt = (m + 31) / 32;
+            // ---- 1. Gram products.  The rows are cut into two halves at h0 (a multiple of
+            // 32); K tile kt holds rows kt*32.. of the first half in tile rows 0..63 and the
+            // same rows of the second half in tile rows 64..127, and the 128 x 128 product
+            // of the tile with itself has Y1^T Y1 and Y2^T Y2 on its diagonal blocks:
+            // P = Y^T Y is their sum.  Every tile row carries data, and the MMA count is
+            // half of what a 64-row tile padded to M = 128 would need.  Two tile buffers.
+            const int nkt = (m + 63) / 64, h0 = 32 * nkt;
             for (int kt = 0; kt < nkt; ++kt) {
                 const int b = kt & 1;
                 if (tid == 0) s_ok = wait_bar(b, lim);   // the products of tile kt - 2 read this buffer
@@ -262,20 +281,25 @@ k_jacobi_tc(const GateDesc* __restrict__ gd, int n_gates, int n_lead, double tol
                 unsigned char* hi = sm + OFF_T + b * 2 * TILE128;
                 unsigned char* lo = hi + TILE128;
                 {
-                    const int c = tid >> 4, rr = (tid & 15) * 2, row = kt * 32 + rr;
-                    float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (valid(c) && row < m) x = *reinterpret_cast<const float4*>(Xs + (size_t)c * m + row);
-                    st_split(hi, lo, sw128_off(c, rr), x.x);
-                    st_split(hi, lo, sw128_off(c, rr + 1), x.z);
-                    st_split(hi, lo, sw128_off(GC + c, rr), x.y);
-                    st_split(hi, lo, sw128_off(GC + c, rr + 1), x.w);
+                    const int c = tid >> 4, rr = (tid & 15) * 2;
+                    const bool vc = valid(c);
+#pragma unroll
+                    for (int half = 0; half < 2; ++half) {
+                        const int row = half * h0 + kt * 32 + rr, t0 = half * 2 * GC;
+                        float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (vc && row < m) x = *reinterpret_cast<const float4*>(Xs + (size_t)c * m + row);
+                        st_split(hi, lo, sw128_off(t0 + c, rr), x.x);
+                        st_split(hi, lo, sw128_off(t0 + c, rr + 1), x.z);
+                        st_split(hi, lo, sw128_off(t0 + GC + c, rr), x.y);
+                        st_split(hi, lo, sw128_off(t0 + GC + c, rr + 1), x.w);
+                    }
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 __syncthreads();
                 if (tid == 0) {
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     const uint32_t ah = sbase + OFF_T + b * 2 * TILE128, al = ah + TILE128;
-                    mma_ktile(t_gram, ah, al, ah, al, idesc, kt == 0);
+                    mma_ktile(t_gram, ah, al, ah, al, idesc_g, kt == 0);
                     mma_commit(b ? bar1 : bar0);
                     pend[b] = true;
                 }
@@ -287,77 +311,77 @@ k_jacobi_tc(const GateDesc* __restrict__ gd, int n_gates, int n_lead, double tol
             }
             if (!fail) {
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                if (warp < 2) {
+                if (warp < 4) {
+                    // warps 0-1: rows 0..63, columns 0..63 (Y1^T Y1); warps 2-3: rows 64..127,
+                    // columns 64..127 (Y2^T Y2), into two staging arrays
                     const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
-                    float* prow = Ps + (warp * 32 + lane) * 65;
+                    const int r = (warp & 1) * 32 + lane, c0 = (warp >> 1) * 64;
+                    float* prow = Ps + (warp >> 1) * 64 * 65 + r * 65;
 #pragma unroll
-                    for (int c0 = 0; c0 < 64; c0 += 16) {
+                    for (int cc = 0; cc < 64; cc += 16) {
                         float vv[16];
-                        tmem_ld16(t_gram + lane_off + c0, vv);
+                        tmem_ld16(t_gram + lane_off + c0 + cc, vv);
 #pragma unroll
-                        for (int e = 0; e < 16; ++e) prow[c0 + e] = vv[e];
+                        for (int e = 0; e < 16; ++e) prow[cc + e] = vv[e];
                     }
                 }
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 __syncthreads();
+                const float* P2 = Ps + 64 * 65;
                 for (int e = tid; e < GC * GC; e += GT) {
                     const int i = e >> 5, j = e & 31;
-                    const float gr = Ps[i * 65 + j] + Ps[(GC + i) * 65 + GC + j];
-                    const float gi = Ps[i * 65 + GC + j] - Ps[(GC + i) * 65 + j];
+                    const float gr = (Ps[i * 65 + j] + P2[i * 65 + j]) + (Ps[(GC + i) * 65 + GC + j] + P2[(GC + i) * 65 + GC + j]);
+                    const float gi = (Ps[i * 65 + GC + j] + P2[i * 65 + GC + j]) - (Ps[(GC + i) * 65 + j] + P2[(GC + i) * 65 + j]);
                     Gb[i * GS + j] = make_float2(gr, gi);
                     Ds[i * GS + j] = make_float2(0.f, 0.f);
                 }
                 __syncthreads();
             }
             // ---- 2. the visit's rotations on G, accumulated in D = V - I
-            int cur = 0, nstep = 0;
+            int cur = 0;
+            // One barrier per step: every warp computes all 16 pairs' rotation parameters
+            // (lane w and lane w + 16: pair w; the same inputs and instructions in every
+            // warp, so every warp reaches the same results and the same skip decision)
+            // and hands them to its threads by shuffles.  A step that rotates nothing
+            // changes nothing and needs no barrier.
             auto run_step = [&](int step, bool stin) {
-                const int sp = nstep++ & 1;
-                PairPrm* prm = s_prm[sp];
-                int* ix = s_ix[sp];
-                if (warp == 0) {
-                    int rot = 0, exam = 0;
-                    if (lane < GB) {
-                        int q1, q2;
-                        pair_of(lane, step, stin, q1, q2);
-                        PairPrm pr{0.f, 0.f, 0.f, 0.f, q1, q2, 0};
-                        if (valid(q1) && valid(q2)) {
-                            exam = 1;
-                            const float2* G = Gb + cur * GC * GS;
-                            const float2 gq = G[q1 * GS + q2];
-                            rot = rot_params_fast(G[q1 * GS + q1].x, G[q2 * GS + q2].x, gq.x, gq.y, tol2, zthr, pr.cm1,
-                                                  pr.sr, pr.si, pr.tg);
-                            pr.rot = rot;
-                        }
-                        prm[lane] = pr;
-                        ix[q1] = 2 * lane;
-                        ix[q2] = 2 * lane + 1;
-                    }
-                    const unsigned rb = __ballot_sync(0xffffffffu, rot), eb = __ballot_sync(0xffffffffu, exam);
-                    if (lane == 0) {
-                        s_any[sp] = rb != 0u;
-                        s_rot += __popc(rb);
-                        s_vis += __popc(eb);
-                    }
+                const float2* G = Gb + cur * GC * GS;
+                int q1w, q2w;
+                pair_of(lane & (GB - 1), step, stin, q1w, q2w);
+                const bool exam = valid(q1w) && valid(q2w);
+                float cmw = 0.f, srw = 0.f, siw = 0.f, tgw = 0.f;
+                int rot = 0;
+                if (exam) {
+                    const float2 gq = G[q1w * GS + q2w];
+                    rot = rot_params_fast(G[q1w * GS + q1w].x, G[q2w * GS + q2w].x, gq.x, gq.y, tol2, zthr, cmw, srw,
+                                          siw, tgw);
                 }
-                __syncthreads();
-                if (!s_any[sp]) return;   // G and D unchanged
+                const unsigned rb = __ballot_sync(0xffffffffu, rot), eb = __ballot_sync(0xffffffffu, exam);
+                if (tid == 0) {
+                    s_rot += __popc(rb & 0xffffu);
+                    s_vis += __popc(eb & 0xffffu);
+                }
+                if (rb == 0u) return;   // G and D unchanged
                 // thread: row p of G and D, the two columns q1 < q2 of pair w
                 const int p = tid >> 4, w = tid & 15;
-                const PairPrm qw = prm[w];
-                const int pix = ix[p];
-                const PairPrm pw = prm[pix >> 1];
-                const bool psec = pix & 1;
-                const int pp = psec ? pw.q1 : pw.q2;
+                int wp, psec;
+                pair_index(p, step, stin, wp, psec);
+                const float cq0 = __shfl_sync(0xffffffffu, cmw, w), sr = __shfl_sync(0xffffffffu, srw, w);
+                const float si = __shfl_sync(0xffffffffu, siw, w), tq = __shfl_sync(0xffffffffu, tgw, w);
+                const int rq = __shfl_sync(0xffffffffu, rot, w);
+                const int q1 = __shfl_sync(0xffffffffu, q1w, w), q2 = __shfl_sync(0xffffffffu, q2w, w);
+                const float cp0 = __shfl_sync(0xffffffffu, cmw, wp), srp = __shfl_sync(0xffffffffu, srw, wp);
+                const float sip = __shfl_sync(0xffffffffu, siw, wp);
+                const int rp = __shfl_sync(0xffffffffu, rot, wp);
+                const int p1 = __shfl_sync(0xffffffffu, q1w, wp), p2 = __shfl_sync(0xffffffffu, q2w, wp);
+                const int pp = psec ? p1 : p2;
                 // J_{q2 q1} = -conj(s e), J_{q1 q2} = s e, J_qq = 1 + cm1 (zero factors if not rotated)
-                const float cq = qw.rot ? qw.cm1 : 0.f;
-                const float2 off1 = qw.rot ? make_float2(-qw.sr, qw.si) : make_float2(0.f, 0.f);
-                const float2 off2 = qw.rot ? make_float2(qw.sr, qw.si) : make_float2(0.f, 0.f);
-                const float cp = pw.rot ? pw.cm1 : 0.f;
-                const float2 offp = pw.rot ? (psec ? make_float2(pw.sr, pw.si) : make_float2(-pw.sr, pw.si))
-                                           : make_float2(0.f, 0.f);   // J_{p' p}
-                const int q1 = qw.q1, q2 = qw.q2;
-                const float2* G = Gb + cur * GC * GS;
+                const float cq = rq ? cq0 : 0.f;
+                const float2 off1 = rq ? make_float2(-sr, si) : make_float2(0.f, 0.f);
+                const float2 off2 = rq ? make_float2(sr, si) : make_float2(0.f, 0.f);
+                const float cp = rp ? cp0 : 0.f;
+                const float2 offp = rp ? (psec ? make_float2(srp, sip) : make_float2(-srp, sip))
+                                       : make_float2(0.f, 0.f);   // J_{p' p}
                 float2* Gn = Gb + (cur ^ 1) * GC * GS;
                 const float2 a1 = G[p * GS + q1], a2 = G[p * GS + q2];
                 const float2 b1 = G[pp * GS + q1], b2 = G[pp * GS + q2];
@@ -367,16 +391,16 @@ k_jacobi_tc(const GateDesc* __restrict__ gd, int n_gates, int n_lead, double tol
                 // (J^H G J)_{pq} = G_pq + [H_pq + cm1_p (G J)_pq + conj(J_{p'p}) (G J)_{p'q}]
                 float2 n1 = cadd(a1, cadd(cadd(ha1, cscale(cp, cadd(a1, ha1))), cmulc(offp, cadd(b1, hb1))));
                 float2 n2 = cadd(a2, cadd(cadd(ha2, cscale(cp, cadd(a2, ha2))), cmulc(offp, cadd(b2, hb2))));
-                if (qw.rot && p == q1) {
-                    n1 = make_float2(a1.x - qw.tg, 0.f);
+                if (rq && p == q1) {
+                    n1 = make_float2(a1.x - tq, 0.f);
                     n2 = make_float2(0.f, 0.f);
-                } else if (qw.rot && p == q2) {
+                } else if (rq && p == q2) {
                     n1 = make_float2(0.f, 0.f);
-                    n2 = make_float2(a2.x + qw.tg, 0.f);
+                    n2 = make_float2(a2.x + tq, 0.f);
                 }
                 Gn[p * GS + q1] = n1;
                 Gn[p * GS + q2] = n2;
-                if (qw.rot) {
+                if (rq) {
                     // D <- D J + (J - I), in place (this thread alone owns D[p][q1], D[p][q2])
                     const float2 d1 = Ds[p * GS + q1], d2 = Ds[p * GS + q2];
                     float2 c1 = cadd(cscale(cq, d1), cmul(d2, off1));
@@ -399,6 +423,7 @@ k_jacobi_tc(const GateDesc* __restrict__ gd, int n_gates, int n_lead, double tol
                     for (int t = 0; t < GB - 1; ++t) run_step(t, true);
                 if (J >= 0)
                     for (int sft = 0; sft < GB; ++sft) run_step(sft, false);
+                __syncthreads();   // s_rot complete; the last steps may have needed no barrier
             }
             // ---- 3. X <- X + X D on the tensor cores (only if anything rotated)
             if (!fail && s_rot > 0) {
@@ -520,7 +545,7 @@ k_jacobi_tc(const GateDesc* __restrict__ gd, int n_gates, int n_lead, double tol
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(s_tmem), "r"(128));
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(s_tmem), "r"(256));
 }
 
 // Launch: one CTA of 512 threads per SM (about 222 KB of shared memory); no more CTAs
